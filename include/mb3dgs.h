@@ -1,0 +1,207 @@
+/*
+ * mb3dgs.h -- C ABI of the GB300 moment-based Gaussian rasterizer.
+ *
+ * Implements the rendering hot path of "Moment-Based 3D Gaussian Splatting"
+ * (MB3DGS, arXiv 2512.11800): a two-pass, sort-free tile rasterizer in which
+ *   (a) every pixel accumulates the analytic density moments of all Gaussians
+ *       covering it (Sec. 3.2, Eq. 10-12, App. C),
+ *   (b) every pixel reconstructs a transmittance function from its moments
+ *       via moment bounds (Sec. 3.2, Eq. 8), and
+ *   (c) a second pass evaluates the per-Gaussian quadrature of the volume
+ *       rendering integral (Eq. 7, App. B) and rescales the opacity (Eq. 15),
+ * plus the adjoint of both passes (Sec. 3.3 "Adjoint Rendering", Eq. 22).
+ *
+ * Conventions (all calls):
+ *  - Every pointer named d_* or documented "device" is CUDA device memory owned
+ *    by the caller; the library never allocates or frees device memory.
+ *  - Calls are asynchronous on the given stream unless documented otherwise.
+ *  - Cameras are OpenCV pinholes (x right, y down, z forward); viewmat is the
+ *    4x4 row-major world->camera transform; pixel (x, y) has its centre at
+ *    (x + 0.5, y + 0.5); ray directions are unit vectors, so ray distances t
+ *    are metric.
+ *  - Gaussians are float32 structure-of-arrays: means[P][3], scales[P][3]
+ *    (positive), quats[P][4] (w,x,y,z, normalised inside), weights[P] (peak
+ *    density w >= 0), sh[P][K][3] with K = (sh_degree+1)^2, sh_degree <= 3.
+ *  - Images are row-major; rgb is [H][W][3], transmittance/penalty [H][W];
+ *    with several views the per-view images are concatenated in view order.
+ *  - The staged calls (bin_tiles .. shade, backward, debug) must be given the
+ *    same cfg, cameras, P and pair_capacity as the mb3dgs_preprocess (or
+ *    mb3dgs_render) call that filled the workspace; the workspace layout is a
+ *    pure function of those values.
+ *  - Return value: MB3DGS_OK (0) or a negative MB3DGS_ERR_* code; nothing
+ *    aborts the process.  Errors detected on the device (pair-capacity
+ *    overflow, non-finite inputs in strict mode) are recorded in a status word
+ *    inside the workspace and read with mb3dgs_get_status().
+ */
+#ifndef MB3DGS_H
+#define MB3DGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mb3dgs_stream_t; /* == cudaStream_t; NULL = legacy default stream */
+
+enum {
+    MB3DGS_OK = 0,
+    MB3DGS_ERR_INVALID_ARG = -1,       /* null pointer, bad size, bad config value */
+    MB3DGS_ERR_CUDA = -2,              /* a CUDA launch or copy failed */
+    MB3DGS_ERR_WORKSPACE_TOO_SMALL = -3,
+    MB3DGS_ERR_TIMEOUT = -4,           /* a bounded device wait expired */
+    MB3DGS_ERR_NUMERIC = -5,           /* non-finite Gaussian parameters seen with strict = 1 */
+    MB3DGS_ERR_UNSUPPORTED = -6,       /* configuration outside what the kernels implement */
+    MB3DGS_ERR_CAPACITY = -7           /* tile-pair count exceeded the workspace's pair capacity */
+};
+
+enum { MB3DGS_MOMENTS_F32 = 0, MB3DGS_MOMENTS_BF16 = 1, MB3DGS_MOMENTS_F16 = 2 };
+enum { MB3DGS_MAX_VIEWS = 32 };
+
+/* Method parameters.  Defaults (mb3dgs_config_default) are the paper's values
+ * where it prints them and documented readings where it does not. */
+typedef struct mb3dgs_config {
+    int n;              /* 2n+1 power moments; n = 4 (Sec. 3.2).  Only 4 is implemented. */
+    int n_intervals;    /* N quadrature intervals, N+1 sample points (Eq. 7); 1..8, default 3 */
+    float kappa;        /* sample spacing t_j = mu + kappa Sigma x_j (App. B); 3 */
+    float beta;         /* tau = m0 ((1-beta) L + beta U) (Sec. 3.2); 0.25 */
+    float conf_c;       /* proxy confidence level c (App. C); 0.01 */
+    float warp_lambda;  /* power-transform lambda of the depth warp (Sec. 3.2); -1.5 */
+    float t_near;       /* t_n; 0.01 (reading) */
+    float t_far;        /* t_f; 1e6 (App. C) */
+    float eps;          /* rescaling clamp of Eq. 15; 1e-6 */
+    float bias_alpha;   /* moment bias towards U[0,1] moments (reading); 1e-3 */
+    float m_min;        /* pixels with m0 < m_min have tau == 0; 1e-7 */
+    float r_mult;       /* culling sphere radius = r_mult * max(scale) (Sec. 3.3); 3 */
+    float bg[3];        /* background radiance L_bg (Eq. 2); black */
+    int moment_dtype;   /* storage of the per-pixel moment buffer: MB3DGS_MOMENTS_* */
+    int strict;         /* 1: non-finite Gaussian parameters set MB3DGS_ERR_NUMERIC */
+} mb3dgs_config;
+
+/* Device pointers, caller-owned, layout as in the file comment. */
+typedef struct mb3dgs_gaussians {
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* weights;
+    const float* sh;
+    int64_t P;
+    int sh_degree;
+} mb3dgs_gaussians;
+
+/* Host struct (passed by value into kernels). */
+typedef struct mb3dgs_camera {
+    float viewmat[16];   /* world -> camera, row-major 4x4 */
+    float fx, fy, cx, cy;
+    int width, height;
+} mb3dgs_camera;
+
+/* Parameter gradients, device, same shapes as mb3dgs_gaussians; written (not
+ * accumulated) by mb3dgs_backward. */
+typedef struct mb3dgs_gaussian_grads {
+    float* means;
+    float* scales;
+    float* quats;
+    float* weights;
+    float* sh;
+} mb3dgs_gaussian_grads;
+
+const char* mb3dgs_status_string(int code);
+
+/* Text of the CUDA error behind the calling thread's last MB3DGS_ERR_CUDA. */
+const char* mb3dgs_last_cuda_error(void);
+
+/* Fills *cfg with the defaults listed above. */
+int mb3dgs_config_default(mb3dgs_config* cfg);
+
+/* Bytes of device workspace needed to render n_views cameras of P Gaussians
+ * with room for pair_capacity (tile, Gaussian) pairs.  Host only. */
+int mb3dgs_workspace_size(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                          int64_t pair_capacity, size_t* bytes);
+
+/* Stage 1 -- per (view, Gaussian): frustum culling with the bounding sphere
+ * (Sec. 3.3), camera-space ray-parameterisation coefficients of Eq. 4-6
+ * (App. A), SH emission (Sec. 3.1), the confidence-interval proxy ellipse and
+ * its pixel rectangle (Eq. 17-21, App. C) and its tile count.  Computed in
+ * FP64, stored FP32.  Resets the workspace status word. */
+int mb3dgs_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
+                      int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity, mb3dgs_stream_t stream);
+
+/* Stage 2 -- tile binning by tile key only, no depth sort: exclusive scan of
+ * the tile counts, emission of (tile, Gaussian) pairs and a stable LSD radix
+ * sort by tile, so each tile's list holds ascending Gaussian ids.  Sets
+ * MB3DGS_ERR_CAPACITY in the status word (and renders nothing) if the pair
+ * count exceeds the capacity given to mb3dgs_preprocess. */
+int mb3dgs_bin_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                     int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream);
+
+/* Stage 3 -- moment pass (Sec. 3.3, App. C): per pixel, sum over the Gaussians
+ * whose rectangle contains the pixel centre of the analytic moments
+ * (Eq. 10-12).  Accumulated in FP32 in an orthonormal Legendre basis of the
+ * warped depth (same moment space as the paper's power moments) and stored
+ * in the workspace with cfg->moment_dtype.  If d_moments_out != NULL it also
+ * receives the paper's power moments m-hat_0..m-hat_2n, layout
+ * [pixel][2n+1] over all views. */
+int mb3dgs_accumulate_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                              int64_t pair_capacity, void* ws, size_t ws_bytes, float* d_moments_out,
+                              mb3dgs_stream_t stream);
+
+/* Stage 4 -- per-pixel reconstruction (Sec. 3.2, Eq. 8): normalise and bias
+ * the moments, compute the recurrence (Jacobi) coefficients of the moment
+ * measure's orthogonal polynomials and its Gauss nodes, stored in the
+ * workspace for the shading pass.  If Q > 0 it also evaluates the
+ * transmittance T(eta) = exp(-tau(eta)), tau = m0 ((1-beta) L + beta U), at
+ * the warped depths d_eta[pixel][Q] into d_T_out[pixel][Q]. */
+int mb3dgs_reconstruct_transmittance(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views,
+                                     int64_t P, int64_t pair_capacity, void* ws, size_t ws_bytes,
+                                     const float* d_eta, int Q, float* d_T_out, mb3dgs_stream_t stream);
+
+/* Stage 5 -- quadrature pass (Eq. 7, App. B) with the consistency penalty
+ * (App. D) and the opacity rescaling epilogue (Eq. 15).  Writes d_rgb
+ * [pixel][3], d_T_final [pixel] = exp(-m0) and, if non-NULL, d_penalty
+ * [pixel] = sum_i P_i.  Keeps sum_i L_i and O in the workspace for backward. */
+int mb3dgs_shade(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                 int64_t pair_capacity, void* ws, size_t ws_bytes, float* d_rgb, float* d_T_final,
+                 float* d_penalty, mb3dgs_stream_t stream);
+
+/* Stages 1-5 in order on one stream; no host synchronisation. */
+int mb3dgs_render(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
+                  void* ws, size_t ws_bytes, int64_t pair_capacity, float* d_rgb, float* d_T_final,
+                  float* d_penalty, mb3dgs_stream_t stream);
+
+/* Adjoint of mb3dgs_render (Sec. 3.3 "Adjoint Rendering", Eq. 22, App. C):
+ * an adjoint-moment pass producing per-pixel dL/dm, then a gradient pass
+ * reducing per-Gaussian gradients over covered pixels, then the chain rule
+ * through the preprocessing to the Gaussian parameters.  Requires the
+ * workspace of the matching mb3dgs_render call (same cfg, g, cams).
+ * d_dL_drgb [pixel][3]; d_dL_dpenalty [pixel] or NULL.  The proxy rectangles
+ * and culling are treated as constants. */
+int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
+                    int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
+                    const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream);
+
+/* Synchronises the stream and reads the workspace status word (an MB3DGS_*
+ * code) and the number of (tile, Gaussian) pairs of the last binning. */
+int mb3dgs_get_status(const void* ws, size_t ws_bytes, int* status, int64_t* n_pairs, mb3dgs_stream_t stream);
+
+/* Debug/test access (device outputs, async): the sorted Gaussian ids of all
+ * tile lists d_ids[capacity], per-tile [start, end) d_ranges[n_tiles][2]
+ * (tiles of all views, row-major per view), and per (view, Gaussian)
+ * integer pixel rectangles d_rects[n_views*P][4] = x0, y0, x1, y1 inclusive
+ * (x0 > x1 when culled).  Any output pointer may be NULL. */
+int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                            int64_t pair_capacity, const void* ws, size_t ws_bytes, int32_t* d_ids,
+                            int32_t* d_ranges, int32_t* d_rects, mb3dgs_stream_t stream);
+
+/* Total number of CUDA kernels this library has launched in the process
+ * (host counter; used to report launches per step). */
+int64_t mb3dgs_launch_count(void);
+
+/* Number of 16x16 tiles over all views (host only). */
+int64_t mb3dgs_num_tiles(const mb3dgs_camera* cams, int n_views);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MB3DGS_H */

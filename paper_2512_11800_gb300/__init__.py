@@ -1,0 +1,221 @@
+"""GB300-native moment-based Gaussian rasterizer (MB3DGS hot path).
+
+Thin Python layer over the C ABI of ``include/mb3dgs.h``: it only marshals
+arguments, owns device memory through PyTorch tensors and passes PyTorch's
+current CUDA stream.  Every step of the rendering path runs in the sm_103a
+kernels of ``libmb3dgs.so``; if the library cannot be loaded the import of
+the rendering functions raises (there is no CPU or PyTorch fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+__all__ = ["RasterConfig", "GaussianTensors", "Rasterizer", "to_camera", "load_library"]
+
+
+def load_library():
+    return B.load()
+
+
+@dataclass
+class RasterConfig:
+    n: int = 4
+    n_intervals: int = 3
+    kappa: float = 3.0
+    beta: float = 0.25
+    conf_c: float = 0.01
+    warp_lambda: float = -1.5
+    t_near: float = 0.01
+    t_far: float = 1.0e6
+    eps: float = 1.0e-6
+    bias_alpha: float = 1.0e-3
+    m_min: float = 1.0e-7
+    r_mult: float = 3.0
+    bg: tuple = (0.0, 0.0, 0.0)
+    moment_dtype: str = "f32"
+    strict: int = 0
+
+    def to_c(self) -> B.Config:
+        c = B.Config()
+        for f in ["n", "n_intervals", "strict"]:
+            setattr(c, f, int(getattr(self, f)))
+        for f in ["kappa", "beta", "conf_c", "warp_lambda", "t_near", "t_far", "eps", "bias_alpha", "m_min", "r_mult"]:
+            setattr(c, f, float(getattr(self, f)))
+        c.bg = B.c_float3(*[float(x) for x in self.bg])
+        c.moment_dtype = B.MOMENTS[self.moment_dtype]
+        return c
+
+
+@dataclass
+class GaussianTensors:
+    """Float32 CUDA tensors: means (P,3), scales (P,3), quats (P,4), weights (P,), sh (P,K,3)."""
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    weights: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @property
+    def P(self):
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda"):
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=device)
+        return GaussianTensors(t(scene.means), t(scene.scales), t(scene.quats), t(scene.weights), t(scene.sh),
+                               int(scene.sh_degree))
+
+    def to_c(self) -> B.Gaussians:
+        for name in ["means", "scales", "quats", "weights", "sh"]:
+            x = getattr(self, name)
+            if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()):
+                raise ValueError("%s must be a contiguous float32 CUDA tensor" % name)
+        g = B.Gaussians()
+        g.means, g.scales, g.quats = self.means.data_ptr(), self.scales.data_ptr(), self.quats.data_ptr()
+        g.weights, g.sh = self.weights.data_ptr(), self.sh.data_ptr()
+        g.P = self.P
+        g.sh_degree = int(self.sh_degree)
+        return g
+
+
+def to_camera(cam) -> B.Camera:
+    """Any object with viewmat (4x4), fx, fy, cx, cy, width, height."""
+    c = B.Camera()
+    vm = np.asarray(cam.viewmat, dtype=np.float32).reshape(16)
+    c.viewmat = (C.c_float * 16)(*vm.tolist())
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Rasterizer:
+    """Renders Gaussians through the C ABI.  Holds a reusable workspace."""
+
+    def __init__(self, config: RasterConfig | None = None, device="cuda"):
+        self.lib = B.load()
+        self.config = config or RasterConfig()
+        self.cfg_c = self.config.to_c()
+        self.device = torch.device(device)
+        self._ws = None
+
+    # ------------------------------------------------------------ plumbing
+    def cameras(self, cams):
+        cams = list(cams) if isinstance(cams, (list, tuple)) else [cams]
+        arr = (B.Camera * len(cams))(*[to_camera(c) for c in cams])
+        return arr, len(cams)
+
+    def workspace_bytes(self, cams, P, capacity):
+        arr, nv = self.cameras(cams)
+        n = C.c_size_t(0)
+        B.check(self.lib.mb3dgs_workspace_size(C.byref(self.cfg_c), arr, nv, int(P), int(capacity), C.byref(n)),
+                "workspace_size")
+        return int(n.value)
+
+    def workspace(self, nbytes):
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def num_pixels(self, cams):
+        cams = list(cams) if isinstance(cams, (list, tuple)) else [cams]
+        return sum(int(c.width) * int(c.height) for c in cams)
+
+    def num_tiles(self, cams):
+        arr, nv = self.cameras(cams)
+        return int(self.lib.mb3dgs_num_tiles(arr, nv))
+
+    def status(self, stream=None):
+        st = C.c_int(0)
+        n = C.c_int64(0)
+        B.check(self.lib.mb3dgs_get_status(_ptr(self._ws), self._ws.numel(), C.byref(st), C.byref(n),
+                                           _stream(stream)), "get_status")
+        return int(st.value), int(n.value)
+
+    # ------------------------------------------------------------ API
+    def count_pairs(self, g: GaussianTensors, cams, stream=None):
+        """(tile, Gaussian) pairs of this frame: preprocess + binning with zero
+        capacity, then one host read of the pair total."""
+        arr, nv = self.cameras(cams)
+        ws = self.workspace(self.workspace_bytes(cams, g.P, 0))
+        gc = g.to_c()
+        s = _stream(stream)
+        B.check(self.lib.mb3dgs_preprocess(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(), 0, s),
+                "preprocess")
+        B.check(self.lib.mb3dgs_bin_tiles(C.byref(self.cfg_c), arr, nv, g.P, 0, _ptr(ws), ws.numel(), s), "bin_tiles")
+        return self.status(stream)[1]
+
+    def render(self, g: GaussianTensors, cams, capacity=None, stream=None, penalty=True, out=None):
+        """Full forward (mb3dgs_render).  Returns dict(rgb (Npix,3), T (Npix,),
+        penalty (Npix,)) over the concatenated views."""
+        arr, nv = self.cameras(cams)
+        if capacity is None:
+            capacity = self.count_pairs(g, cams, stream)
+        nbytes = self.workspace_bytes(cams, g.P, capacity)
+        ws = self.workspace(nbytes)
+        npix = self.num_pixels(cams)
+        if out is None:
+            out = dict(rgb=torch.empty(npix, 3, device=self.device), T=torch.empty(npix, device=self.device),
+                       penalty=torch.empty(npix, device=self.device) if penalty else None)
+        gc = g.to_c()
+        B.check(self.lib.mb3dgs_render(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(), int(capacity),
+                                       _ptr(out["rgb"]), _ptr(out["T"]), _ptr(out.get("penalty")), _stream(stream)),
+                "render")
+        out["capacity"] = int(capacity)
+        return out
+
+    def render_staged(self, g: GaussianTensors, cams, capacity=None, eta=None, stream=None):
+        """The five stage calls one by one; also returns the power moments
+        (Npix, 9), the transmittance at the warped depths ``eta`` (Npix, Q) and
+        the tile lists for inspection."""
+        arr, nv = self.cameras(cams)
+        if capacity is None:
+            capacity = self.count_pairs(g, cams, stream)
+        ws = self.workspace(self.workspace_bytes(cams, g.P, capacity))
+        npix = self.num_pixels(cams)
+        s = _stream(stream)
+        cfg = C.byref(self.cfg_c)
+        gc = g.to_c()
+        P = g.P
+        B.check(self.lib.mb3dgs_preprocess(cfg, C.byref(gc), arr, nv, _ptr(ws), ws.numel(), int(capacity), s),
+                "preprocess")
+        B.check(self.lib.mb3dgs_bin_tiles(cfg, arr, nv, P, int(capacity), _ptr(ws), ws.numel(), s), "bin_tiles")
+        mom = torch.empty(npix, 9, device=self.device)
+        B.check(self.lib.mb3dgs_accumulate_moments(cfg, arr, nv, P, int(capacity), _ptr(ws), ws.numel(), _ptr(mom), s),
+                "accumulate_moments")
+        Tq = None
+        Q = 0
+        if eta is not None:
+            eta = eta.contiguous().float()
+            Q = int(eta.shape[1])
+            Tq = torch.empty(npix, Q, device=self.device)
+        B.check(self.lib.mb3dgs_reconstruct_transmittance(cfg, arr, nv, P, int(capacity), _ptr(ws), ws.numel(),
+                                                          _ptr(eta), Q, _ptr(Tq), s), "reconstruct")
+        rgb = torch.empty(npix, 3, device=self.device)
+        T = torch.empty(npix, device=self.device)
+        pen = torch.empty(npix, device=self.device)
+        B.check(self.lib.mb3dgs_shade(cfg, arr, nv, P, int(capacity), _ptr(ws), ws.numel(), _ptr(rgb), _ptr(T),
+                                      _ptr(pen), s), "shade")
+        ntiles = self.num_tiles(cams)
+        ids = torch.empty(max(int(capacity), 1), dtype=torch.int32, device=self.device)
+        ranges = torch.empty(ntiles, 2, dtype=torch.int32, device=self.device)
+        rects = torch.empty(nv * P, 4, dtype=torch.int32, device=self.device)
+        B.check(self.lib.mb3dgs_debug_tile_lists(cfg, arr, nv, P, int(capacity), _ptr(ws), ws.numel(), _ptr(ids),
+                                                 _ptr(ranges), _ptr(rects), s), "debug_tile_lists")
+        return dict(rgb=rgb, T=T, penalty=pen, moments=mom, T_eta=Tq, ids=ids[:capacity], ranges=ranges, rects=rects,
+                    capacity=int(capacity))

@@ -1,0 +1,397 @@
+// C ABI entry points (include/mb3dgs.h): argument validation, workspace
+// layout, kernel parameters and launch order.  No device allocation.
+#include <cmath>
+#include <atomic>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace mb {
+void launch_preprocess(const Params&, const ViewTable&, const mb3dgs_gaussians&, float*, int*, int*,
+                       unsigned long long*, cudaStream_t);
+void launch_binning(const ViewTable&, const Layout&, char*, cudaStream_t);
+size_t scan_tmp_elems(int64_t);
+void launch_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t);
+void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaStream_t);
+void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t);
+void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t);
+int launch_backward(const Params&, const ViewTable&, const Layout&, char*, const mb3dgs_gaussians&, const float*,
+                    const float*, const mb3dgs_gaussian_grads&, cudaStream_t);
+
+struct StatusHost {
+    int status;
+    int pad;
+    long long n_total;
+    long long n_valid;
+    unsigned long long nonfinite;
+};
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Phi^-1(p) by bisection + Newton on Phi(x) = erfc(-x / sqrt 2) / 2 (double)
+static double inv_normal_cdf(double p) {
+    double lo = -12.0, hi = 12.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (0.5 * std::erfc(-mid / std::sqrt(2.0)) < p) lo = mid; else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 3; ++it) {
+        const double f = 0.5 * std::erfc(-x / std::sqrt(2.0)) - p;
+        const double d = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+        x -= f / d;
+    }
+    return x;
+}
+
+static int check_cfg(const mb3dgs_config* c) {
+    if (!c) return MB3DGS_ERR_INVALID_ARG;
+    if (c->n != 4) return MB3DGS_ERR_UNSUPPORTED;
+    if (c->n_intervals < 1 || c->n_intervals > MAX_NODES - 1) return MB3DGS_ERR_UNSUPPORTED;
+    if (!(c->kappa > 0) || !(c->beta >= 0 && c->beta <= 1) || !(c->conf_c > 0 && c->conf_c < 1) ||
+        !(c->t_near > 0) || !(c->t_far > c->t_near) || !(c->eps > 0) || !(c->bias_alpha >= 0 && c->bias_alpha < 1) ||
+        !(c->m_min >= 0) || !(c->r_mult > 0) || c->warp_lambda == 0.0f || c->warp_lambda == 1.0f)
+        return MB3DGS_ERR_INVALID_ARG;
+    if (c->moment_dtype < 0 || c->moment_dtype > 2) return MB3DGS_ERR_INVALID_ARG;
+    return MB3DGS_OK;
+}
+
+static int make_views(const mb3dgs_camera* cams, int n_views, ViewTable& vt, int64_t& npix, int64_t& ntiles) {
+    if (!cams || n_views < 1 || n_views > MB3DGS_MAX_VIEWS) return MB3DGS_ERR_INVALID_ARG;
+    std::memset(&vt, 0, sizeof(vt));
+    vt.n_views = n_views;
+    npix = 0;
+    ntiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const mb3dgs_camera& c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || c.width > 65536 || c.height > 65536 || !(c.fx > 0) || !(c.fy > 0))
+            return MB3DGS_ERR_INVALID_ARG;
+        ViewDesc& d = vt.v[v];
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) d.R[3 * a + b] = c.viewmat[4 * a + b];
+            d.t[a] = c.viewmat[4 * a + 3];
+        }
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        d.width = c.width; d.height = c.height;
+        d.tiles_x = (c.width + TILE - 1) / TILE;
+        d.tiles_y = (c.height + TILE - 1) / TILE;
+        d.tile_base = (int)ntiles;
+        d.pixel_base = npix;
+        ntiles += (int64_t)d.tiles_x * d.tiles_y;
+        npix += (int64_t)c.width * c.height;
+    }
+    if (ntiles >= (int64_t(1) << 31)) return MB3DGS_ERR_INVALID_ARG;
+    return MB3DGS_OK;
+}
+
+static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t npix, int64_t ntiles, int64_t P,
+                       int64_t cap, Layout& L) {
+    if (P < 0 || cap < 0 || cap >= (int64_t(1) << 31)) return MB3DGS_ERR_INVALID_ARG;
+    std::memset(&L, 0, sizeof(L));
+    L.P = P;
+    L.VP = P * vt.n_views;
+    if (L.VP >= (int64_t(1) << 31)) return MB3DGS_ERR_INVALID_ARG;
+    L.npix = npix;
+    L.cap = cap;
+    L.n_tiles = ntiles;
+    L.n_views = vt.n_views;
+    L.nb_sort = (int)std::max<int64_t>(1, ceil_div64(cap, 4096));
+    int bits = 0;
+    while ((int64_t(1) << bits) < ntiles) ++bits;
+    L.sort_passes = (bits + 7) / 8;
+    L.final_buf = L.sort_passes % 2;
+    L.scan_tmp_elems = std::max(scan_tmp_elems(L.VP), scan_tmp_elems((int64_t)256 * L.nb_sort));
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
+    L.status = take(64);
+    L.rec = take(sizeof(float) * REC * (size_t)L.VP);
+    L.counts = take(sizeof(int) * (size_t)L.VP);
+    L.offsets = take(sizeof(int) * (size_t)L.VP);
+    L.scan_tmp = take(sizeof(int) * L.scan_tmp_elems);
+    L.keys[0] = take(sizeof(uint32_t) * (size_t)cap);
+    L.keys[1] = take(sizeof(uint32_t) * (size_t)cap);
+    L.vals[0] = take(sizeof(int32_t) * (size_t)cap);
+    L.vals[1] = take(sizeof(int32_t) * (size_t)cap);
+    L.hist = take(sizeof(uint32_t) * 256 * (size_t)L.nb_sort);
+    L.ranges = take(sizeof(int) * 2 * (size_t)ntiles);
+    const int md = cfg ? cfg->moment_dtype : 0;
+    L.moments = take(md == MB3DGS_MOMENTS_F32 ? sizeof(float) * NMOM * (size_t)npix
+                                              : sizeof(float) * (size_t)npix + 2 * (NMOM - 1) * (size_t)npix);
+    L.recon = take(sizeof(float) * RECON * (size_t)npix);
+    L.saved = take(sizeof(float) * 4 * (size_t)npix);
+    L.dm = take(sizeof(float) * NMOM * (size_t)npix);
+    L.grec = take(sizeof(float) * 16 * (size_t)L.VP);
+    L.total = o;
+    return MB3DGS_OK;
+}
+
+static void make_params(const mb3dgs_config* c, Params& p) {
+    std::memset(&p, 0, sizeof(p));
+    p.n_intervals = c->n_intervals;
+    p.kappa = c->kappa; p.beta = c->beta; p.conf_c = c->conf_c; p.t_near = c->t_near; p.t_far = c->t_far;
+    p.eps = c->eps; p.bias_alpha = c->bias_alpha; p.m_min = c->m_min; p.r_mult = c->r_mult;
+    for (int k = 0; k < 3; ++k) p.bg[k] = c->bg[k];
+    p.warp_lambda = c->warp_lambda;
+    const double lam = c->warp_lambda, a = std::fabs(lam - 1.0);
+    auto f = [&](double x) { return (a / lam) * (std::pow(x / a + 1.0, lam) - 1.0); };
+    const double fn = f(2.0 * c->t_near), ff = f(2.0 * c->t_far);
+    const double G1 = (a / lam) / (ff - fn);
+    p.G1 = (float)G1;
+    p.G0 = (float)((-a / lam - fn) / (ff - fn));
+    p.G2 = (float)(G1 * lam * 2.0 / a);
+    p.two_over_a = (float)(2.0 / a);
+    p.lam_is_m15 = c->warp_lambda == -1.5f;
+    const int N = c->n_intervals;
+    for (int j = 0; j <= N; ++j) p.x_nodes[j] = (float)inv_normal_cdf((j + 0.5) / (N + 1));
+    const double pi = M_PI;
+    const double c0 = 0.5 / std::sqrt(pi), c1 = std::sqrt(3.0 / (4.0 * pi)), c2 = 0.5 * std::sqrt(15.0 / pi),
+                 c20 = 0.25 * std::sqrt(5.0 / pi), c22 = 0.25 * std::sqrt(15.0 / pi),
+                 c33 = 0.25 * std::sqrt(35.0 / (2.0 * pi)), c32 = 0.5 * std::sqrt(105.0 / pi),
+                 c31 = 0.25 * std::sqrt(21.0 / (2.0 * pi)), c30 = 0.25 * std::sqrt(7.0 / pi),
+                 c32b = 0.25 * std::sqrt(105.0 / pi);
+    const double shc[16] = {c0, c1, c1, c1, c2, c2, c20, c2, c22, c33, c32, c31, c30, c31, c32b, c33};
+    for (int k = 0; k < 16; ++k) p.sh_c[k] = (float)shc[k];
+    // u^k = ((1 + y)/2)^k in the Legendre basis: y^j -> Legendre by y P_l = ((l+1) P_{l+1} + l P_{l-1})/(2l+1)
+    double ypow[NMOM][NMOM] = {};  // ypow[j][l]: y^j = sum_l ypow[j][l] P_l
+    ypow[0][0] = 1.0;
+    for (int j = 0; j + 1 < NMOM; ++j)
+        for (int l = 0; l < NMOM; ++l) {
+            const double cf = ypow[j][l];
+            if (cf == 0.0) continue;
+            if (l + 1 < NMOM) ypow[j + 1][l + 1] += cf * (l + 1) / (2.0 * l + 1);
+            if (l >= 1) ypow[j + 1][l - 1] += cf * l / (2.0 * l + 1);
+        }
+    for (int k = 0; k < NMOM; ++k) {
+        double binom = 1.0;
+        for (int j = 0; j <= k; ++j) {
+            if (j > 0) binom = binom * (k - j + 1) / j;
+            for (int l = 0; l < NMOM; ++l) p.leg_to_pow[k * NMOM + l] += (float)(binom * ypow[j][l] / std::pow(2.0, k));
+        }
+    }
+    p.strict = c->strict;
+    p.moment_dtype = c->moment_dtype;
+}
+
+struct Ctx {
+    Params p;
+    ViewTable vt;
+    Layout L;
+};
+
+static int setup(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P, int64_t cap,
+                 size_t ws_bytes, const void* ws, Ctx& c) {
+    int rc = check_cfg(cfg);
+    if (rc) return rc;
+    int64_t npix, ntiles;
+    rc = make_views(cams, n_views, c.vt, npix, ntiles);
+    if (rc) return rc;
+    rc = make_layout(cfg, c.vt, npix, ntiles, P, cap, c.L);
+    if (rc) return rc;
+    if (ws == nullptr && c.L.total > 0) return MB3DGS_ERR_INVALID_ARG;
+    if (ws_bytes < c.L.total) return MB3DGS_ERR_WORKSPACE_TOO_SMALL;
+    make_params(cfg, c.p);
+    return MB3DGS_OK;
+}
+
+static thread_local const char* g_last_cuda_error = "no error";
+static int cuda_ok() {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return MB3DGS_OK;
+    g_last_cuda_error = cudaGetErrorString(e);
+    return MB3DGS_ERR_CUDA;
+}
+
+}  // namespace mb
+
+using namespace mb;
+
+extern "C" {
+
+const char* mb3dgs_status_string(int code) {
+    switch (code) {
+        case MB3DGS_OK: return "ok";
+        case MB3DGS_ERR_INVALID_ARG: return "invalid argument";
+        case MB3DGS_ERR_CUDA: return "CUDA error";
+        case MB3DGS_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+        case MB3DGS_ERR_TIMEOUT: return "device wait timed out";
+        case MB3DGS_ERR_NUMERIC: return "non-finite Gaussian parameters";
+        case MB3DGS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case MB3DGS_ERR_CAPACITY: return "tile-pair capacity exceeded";
+        default: return "unknown status";
+    }
+}
+
+const char* mb3dgs_last_cuda_error(void) { return g_last_cuda_error; }
+
+int mb3dgs_config_default(mb3dgs_config* c) {
+    if (!c) return MB3DGS_ERR_INVALID_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->n = 4;
+    c->n_intervals = 3;
+    c->kappa = 3.0f;
+    c->beta = 0.25f;
+    c->conf_c = 0.01f;
+    c->warp_lambda = -1.5f;
+    c->t_near = 0.01f;
+    c->t_far = 1.0e6f;
+    c->eps = 1.0e-6f;
+    c->bias_alpha = 1.0e-3f;
+    c->m_min = 1.0e-7f;
+    c->r_mult = 3.0f;
+    c->moment_dtype = MB3DGS_MOMENTS_F32;
+    c->strict = 0;
+    return MB3DGS_OK;
+}
+
+int64_t mb3dgs_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int64_t mb3dgs_num_tiles(const mb3dgs_camera* cams, int n_views) {
+    ViewTable vt;
+    int64_t npix, nt;
+    if (make_views(cams, n_views, vt, npix, nt)) return -1;
+    return nt;
+}
+
+int mb3dgs_workspace_size(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                          int64_t pair_capacity, size_t* bytes) {
+    if (!bytes) return MB3DGS_ERR_INVALID_ARG;
+    Ctx c;
+    int rc = check_cfg(cfg);
+    if (rc) return rc;
+    int64_t npix, nt;
+    rc = make_views(cams, n_views, c.vt, npix, nt);
+    if (rc) return rc;
+    rc = make_layout(cfg, c.vt, npix, nt, P, pair_capacity, c.L);
+    if (rc) return rc;
+    *bytes = c.L.total;
+    return MB3DGS_OK;
+}
+
+int mb3dgs_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
+                      void* ws, size_t ws_bytes, int64_t pair_capacity, mb3dgs_stream_t stream) {
+    if (!g || g->P < 0 || g->sh_degree < 0 || g->sh_degree > 3) return MB3DGS_ERR_INVALID_ARG;
+    if (g->P > 0 && (!g->means || !g->scales || !g->quats || !g->weights || !g->sh)) return MB3DGS_ERR_INVALID_ARG;
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, g->P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    if (cudaMemsetAsync(w + c.L.status, 0, 64, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    StatusHost* sw = reinterpret_cast<StatusHost*>(w + c.L.status);
+    launch_preprocess(c.p, c.vt, *g, reinterpret_cast<float*>(w + c.L.rec), reinterpret_cast<int*>(w + c.L.counts),
+                      &sw->status, &sw->nonfinite, st);
+    return cuda_ok();
+}
+
+int mb3dgs_bin_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                     int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream) {
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    launch_binning(c.vt, c.L, static_cast<char*>(ws), reinterpret_cast<cudaStream_t>(stream));
+    return cuda_ok();
+}
+
+int mb3dgs_accumulate_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                              int64_t pair_capacity, void* ws, size_t ws_bytes, float* d_moments_out,
+                              mb3dgs_stream_t stream) {
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    launch_moments(c.p, c.vt, c.L, w, st);
+    if (d_moments_out) launch_moments_to_power(c.p, c.L, w, d_moments_out, st);
+    return cuda_ok();
+}
+
+int mb3dgs_reconstruct_transmittance(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                                     int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_eta, int Q,
+                                     float* d_T_out, mb3dgs_stream_t stream) {
+    if (Q < 0 || (Q > 0 && (!d_eta || !d_T_out))) return MB3DGS_ERR_INVALID_ARG;
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    launch_reconstruct(c.p, c.L, static_cast<char*>(ws), d_eta, Q, d_T_out, reinterpret_cast<cudaStream_t>(stream));
+    return cuda_ok();
+}
+
+int mb3dgs_shade(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P, int64_t pair_capacity,
+                 void* ws, size_t ws_bytes, float* d_rgb, float* d_T_final, float* d_penalty, mb3dgs_stream_t stream) {
+    if (!d_rgb || !d_T_final) return MB3DGS_ERR_INVALID_ARG;
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    launch_shade(c.p, c.vt, c.L, static_cast<char*>(ws), d_rgb, d_T_final, d_penalty,
+                 reinterpret_cast<cudaStream_t>(stream));
+    return cuda_ok();
+}
+
+int mb3dgs_render(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
+                  void* ws, size_t ws_bytes, int64_t pair_capacity, float* d_rgb, float* d_T_final, float* d_penalty,
+                  mb3dgs_stream_t stream) {
+    if (!d_rgb || !d_T_final) return MB3DGS_ERR_INVALID_ARG;
+    int rc = mb3dgs_preprocess(cfg, g, cams, n_views, ws, ws_bytes, pair_capacity, stream);
+    if (rc) return rc;
+    Ctx c;
+    rc = setup(cfg, cams, n_views, g->P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    launch_binning(c.vt, c.L, w, st);
+    launch_moments(c.p, c.vt, c.L, w, st);
+    launch_reconstruct(c.p, c.L, w, nullptr, 0, nullptr, st);
+    launch_shade(c.p, c.vt, c.L, w, d_rgb, d_T_final, d_penalty, st);
+    return cuda_ok();
+}
+
+int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
+                    void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
+                    const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
+    if (!g || !d_dL_drgb || !grads) return MB3DGS_ERR_INVALID_ARG;
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, g->P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    rc = launch_backward(c.p, c.vt, c.L, static_cast<char*>(ws), *g, d_dL_drgb, d_dL_dpenalty, *grads,
+                         reinterpret_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    return cuda_ok();
+}
+
+int mb3dgs_get_status(const void* ws, size_t ws_bytes, int* status, int64_t* n_pairs, mb3dgs_stream_t stream) {
+    if (!ws || ws_bytes < 64) return MB3DGS_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    StatusHost h;
+    if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    if (status) *status = h.status;
+    if (n_pairs) *n_pairs = h.n_total;
+    return MB3DGS_OK;
+}
+
+int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                            int64_t pair_capacity, const void* ws, size_t ws_bytes, int32_t* d_ids, int32_t* d_ranges,
+                            int32_t* d_rects, mb3dgs_stream_t stream) {
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t cap = pair_capacity;
+    const char* w = static_cast<const char*>(ws);
+    if (d_ids && cap > 0)
+        if (cudaMemcpyAsync(d_ids, w + c.L.vals[c.L.final_buf], sizeof(int32_t) * cap, cudaMemcpyDeviceToDevice, st))
+            return MB3DGS_ERR_CUDA;
+    if (d_ranges && c.L.n_tiles > 0)
+        if (cudaMemcpyAsync(d_ranges, w + c.L.ranges, sizeof(int32_t) * 2 * c.L.n_tiles, cudaMemcpyDeviceToDevice, st))
+            return MB3DGS_ERR_CUDA;
+    if (d_rects && c.L.VP > 0)
+        if (cudaMemcpy2DAsync(d_rects, 4 * sizeof(int32_t), w + c.L.rec + sizeof(float) * R_RECT, sizeof(float) * REC,
+                              4 * sizeof(int32_t), (size_t)c.L.VP, cudaMemcpyDeviceToDevice, st))
+            return MB3DGS_ERR_CUDA;
+    return cuda_ok();
+}
+
+}  // extern "C"

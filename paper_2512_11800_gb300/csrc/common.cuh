@@ -1,0 +1,528 @@
+// Shared device code of the GB300 moment-based Gaussian rasterizer.
+//
+// Everything here runs in FP32 except the per-Gaussian preprocessing
+// (preprocess.cu, FP64).  Notation follows "Moment-Based 3D Gaussian
+// Splatting" (MB3DGS): mu, Sigma, w-hat of the ray-parameterised Gaussian
+// (Eq. 4-6), warped depth g-hat (Sec. 3.2), moments (Eq. 10-12), moment
+// bounds L, U (Eq. 8), quadrature (Eq. 7), rescaling (Eq. 15).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mb3dgs.h"
+
+namespace mb {
+
+constexpr int TILE = 16;              // 16x16 pixels per tile, one thread per pixel
+constexpr int TPB = TILE * TILE;      // threads per raster block
+constexpr int NMOM = 9;               // 2n+1 moments, n = 4
+constexpr int NQ = 4;                 // n: roots of the kernel polynomial
+constexpr int REC = 32;               // floats per (view, Gaussian) record
+constexpr int RECON = 20;             // floats per pixel of reconstruction state
+constexpr int MAX_NODES = 9;          // N+1 <= 9 sample points
+constexpr int LAG_ITERS = 6;          // Laguerre iterations per root
+constexpr double OUTER_SPAN = 8.0;   // outer-root search span beyond the Gauss nodes (y units)
+
+// record field offsets (floats)
+enum RecField {
+    R_C0 = 0,    // o_g x g_a (3)
+    R_CX = 3,    // o_g x m_x (3)
+    R_CY = 6,    // o_g x m_y (3)
+    R_Q00 = 9,   // |g_a|^2
+    R_Q01 = 10,  // 2 g_a.m_x
+    R_Q02 = 11,  // 2 g_a.m_y
+    R_Q11 = 12,  // |m_x|^2
+    R_Q12 = 13,  // 2 m_x.m_y
+    R_Q22 = 14,  // |m_y|^2
+    R_O0 = 15,   // o_g.g_a
+    R_OX = 16,   // o_g.m_x
+    R_OY = 17,   // o_g.m_y
+    R_LNW = 18,  // ln w
+    R_RGB = 19,  // SH colour (3)
+    R_AX = 22,   // anchor pixel-centre x (half-integer)
+    R_AY = 23,
+    R_RECT = 24, // int x0, y0, x1, y1 (inclusive pixel range; x0 > x1 = empty)
+    R_FLAGS = 28 // int: bit0 visible, bit1 full-image proxy
+};
+
+struct ViewDesc {
+    float R[9];        // world->camera rotation, row-major
+    float t[3];
+    float fx, fy, cx, cy;
+    int width, height;
+    int tiles_x, tiles_y;
+    int tile_base;     // first global tile index of this view
+    int64_t pixel_base;  // first global pixel index of this view
+};
+
+struct ViewTable {
+    int n_views;
+    ViewDesc v[MB3DGS_MAX_VIEWS];
+};
+
+// Method constants passed by value to every kernel.
+struct Params {
+    int n_intervals;
+    float kappa, beta, conf_c, t_near, t_far, eps, bias_alpha, m_min, r_mult;
+    float bg[3];
+    float warp_lambda;
+    // g-hat(t) = G0 + G1 (1 + 2t/a)^lambda, g-hat'(t) = G2 (1 + 2t/a)^(lambda-1), a = |lambda-1|
+    float G0, G1, G2, two_over_a;
+    int lam_is_m15;        // lambda == -1.5: powers via rsqrt
+    float x_nodes[MAX_NODES];    // standard-normal sample nodes (App. B)
+    float sh_c[16];        // real SH normalisation constants
+    float leg_to_pow[NMOM * NMOM]; // m-hat_k = sum_l leg_to_pow[k*9+l] I_l
+    int strict;
+    int moment_dtype;
+};
+
+// Workspace layout (byte offsets), computed on the host.
+struct Layout {
+    size_t status;      // int32 status; int32 pad; int64 n_pairs_total; int64 n_pairs_valid; int64 n_nonfinite
+    size_t rec;         // float [VP][REC]
+    size_t counts;      // int32 [VP]
+    size_t offsets;     // int32 [VP]
+    size_t scan_tmp;    // int32 scratch for the scans
+    size_t keys[2];     // uint32 [cap] ping-pong
+    size_t vals[2];     // int32  [cap]
+    size_t hist;        // uint32 [256][nb_sort]
+    size_t ranges;      // int32 [T][2]
+    size_t moments;     // F32: float [9][NPIX]; 16-bit: float [NPIX] + u16 [8][NPIX]
+    size_t recon;       // float [RECON][NPIX]
+    size_t saved;       // float [4][NPIX]: sum L (3), O
+    size_t dm;          // float [9][NPIX] adjoint moments (backward)
+    size_t grec;        // float [VP][16] per-record gradients (backward)
+    size_t total;
+    int64_t VP, P, npix, cap;
+    int64_t n_tiles;
+    int nb_sort, sort_passes, final_buf;
+    int n_views;
+    size_t scan_tmp_elems;
+};
+
+__host__ __device__ inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+#define MB_HD __host__ __device__ __forceinline__
+
+MB_HD float rsqrt_(float x) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(x);
+#else
+    return 1.0f / sqrtf(x);
+#endif
+}
+
+// ----------------------------------------------------------------------------
+// warp g-hat and its derivative (Sec. 3.2; power transform with lambda)
+// ----------------------------------------------------------------------------
+MB_HD void warp_g(const Params& p, float t, float& g, float& dg) {
+    float z = fmaf(p.two_over_a, t, 1.0f);
+    float zl, zl1;
+    if (p.lam_is_m15) {
+        float r = rsqrt_(z);
+        zl = r * r * r;          // z^-1.5
+        zl1 = zl / z;            // z^-2.5
+    } else {
+        zl = powf(z, p.warp_lambda);
+        zl1 = zl / z;
+    }
+    g = fmaf(p.G1, zl, p.G0);
+    dg = p.G2 * zl1;
+}
+
+MB_HD float warp_only(const Params& p, float t) {
+    float z = fmaf(p.two_over_a, t, 1.0f);
+    float zl;
+    if (p.lam_is_m15) {
+        float r = rsqrt_(z);
+        zl = r * r * r;
+    } else {
+        zl = powf(z, p.warp_lambda);
+    }
+    return fmaf(p.G1, zl, p.G0);
+}
+
+// ----------------------------------------------------------------------------
+// Ray-parameterised 1D Gaussian of one (pixel, Gaussian) pair (Eq. 4-6).
+// The record holds o_g x d_g, |d_g|^2 and o_g.d_g as polynomials in the pixel
+// offset (dx, dy) from an anchor pixel centre, so the only per-pair rounding is
+// in small, well-conditioned quantities.
+// ----------------------------------------------------------------------------
+struct Gauss1D {
+    float mu, Sig, Sig2, what;
+};
+
+MB_HD Gauss1D pair_gaussian(const float* __restrict__ r, float dx, float dy, float rlen,
+                                                 float r2) {
+    float vx = fmaf(dy, r[R_CY + 0], fmaf(dx, r[R_CX + 0], r[R_C0 + 0]));
+    float vy = fmaf(dy, r[R_CY + 1], fmaf(dx, r[R_CX + 1], r[R_C0 + 1]));
+    float vz = fmaf(dy, r[R_CY + 2], fmaf(dx, r[R_CX + 2], r[R_C0 + 2]));
+    float cross2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    float dd = r[R_Q00] + dx * fmaf(dx, r[R_Q11], r[R_Q01]) + dy * fmaf(dy, r[R_Q22], fmaf(dx, r[R_Q12], r[R_Q02]));
+    float od = fmaf(dy, r[R_OY], fmaf(dx, r[R_OX], r[R_O0]));
+    float inv = 1.0f / dd;
+    Gauss1D g;
+    g.Sig2 = r2 * inv;
+    g.Sig = sqrtf(g.Sig2);
+    g.mu = -od * rlen * inv;
+    g.what = expf(fmaf(-0.5f * cross2, inv, r[R_LNW]));
+    return g;
+}
+
+MB_HD bool rect_contains(const float* __restrict__ r, int px, int py) {
+    const int* ri = reinterpret_cast<const int*>(r + R_RECT);
+    return px >= ri[0] && px <= ri[2] && py >= ri[1] && py <= ri[3];
+}
+
+// ----------------------------------------------------------------------------
+// Moments of one Gaussian in the Legendre basis of y = 2 g-hat - 1 (App. C
+// recurrence, rewritten for P_k): with y_t = A + S (t - mu) the linearised
+// warp, I_k = int_{t_n}^inf P_k(y_t) w-hat e^{-(t-mu)^2/(2 Sigma^2)} dt obeys
+// (k+1) I_{k+1} + k I_{k-1} = (2k+1) [A I_k + S Sigma^2 (P_k(y_n) G_n + S D_k)],
+// D_k = int P_k'(y_t) G dt = sum_{j = k-1, k-3, ..} (2j+1) I_j,
+// and I_0 = m-hat_0 (Eq. 10).  Same moment space as the power moments.
+// ----------------------------------------------------------------------------
+MB_HD void legendre_moments(const Params& p, const Gauss1D& g, float acc[NMOM]) {
+    float a, s;
+    warp_g(p, g.mu, a, s);
+    const float A = fmaf(2.0f, a, -1.0f);
+    const float S = 2.0f * s;
+    const float bn = (p.t_near - g.mu) * (0.70710678118654752f / g.Sig);
+    const float I0 = g.what * g.Sig * 1.25331413731550025f * erfcf(bn);
+    const float Gn = g.what * expf(-bn * bn);
+    const float yn = fmaf(S, p.t_near - g.mu, A);
+    const float SS2 = S * g.Sig2;
+    float Ikm1 = 0.0f, Ik = I0, Pkm1 = 0.0f, Pk = 1.0f, Dkm1 = 0.0f, Dk = 0.0f;
+    acc[0] += I0;
+#pragma unroll
+    for (int k = 0; k < NMOM - 1; ++k) {
+        const float c2k1 = (float)(2 * k + 1);
+        const float inv = 1.0f / (float)(k + 1);
+        float t = fmaf(A, Ik, SS2 * fmaf(Pk, Gn, S * Dk));
+        float In = (c2k1 * t - (float)k * Ikm1) * inv;
+        acc[k + 1] += In;
+        float Pn = (c2k1 * yn * Pk - (float)k * Pkm1) * inv;
+        float Dn = fmaf(c2k1, Ik, Dkm1);
+        Ikm1 = Ik; Ik = In;
+        Pkm1 = Pk; Pk = Pn;
+        Dkm1 = Dk; Dk = Dn;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Per-pixel reconstruction state (Sec. 3.2).  The biased, normalised measure's
+// monic orthogonal polynomials pi_k obey pi_{k+1} = (y - al_k) pi_k - be_k
+// pi_{k-1}; the modified Chebyshev algorithm (Gautschi) gets al, be from the
+// Legendre moments.  The canonical representation through eta is the
+// Gauss-Radau rule with a node at eta; its other nodes are the roots of the
+// kernel polynomial K(x, eta) = sum_k h_k pi_k(x) pi_k(eta), h_k =
+// 1/(be_1..be_k), and they interlace with the Gauss nodes z (roots of pi_4).
+// Weights are 1/K(x, x) (Christoffel).
+// ----------------------------------------------------------------------------
+struct Recon {
+    float m0;
+    float c, inv_s;   // standardisation y' = (y - c) / s, c = al_0, s = sqrt(be_1) (mean / std of the measure)
+    float span;       // outer-root search span (8 y-units) in standardised units
+    float al[4];      // standardised recurrence coefficients (al[0] = 0)
+    float be[4];      // be_1..be_4 (be[0] = 1)
+    float h[4];       // h_1..h_4
+    float z[4];       // Gauss nodes, ascending
+};
+
+MB_HD void pis(const Recon& R, float x, float P[5]) {
+    P[0] = 1.0f;
+    P[1] = x - R.al[0];
+    P[2] = fmaf(x - R.al[1], P[1], -R.be[0] * P[0]);
+    P[3] = fmaf(x - R.al[2], P[2], -R.be[1] * P[1]);
+    P[4] = fmaf(x - R.al[3], P[3], -R.be[2] * P[2]);
+}
+
+MB_HD float kernel_poly(const Recon& R, const float e[5], float x) {
+    float P[5];
+    pis(R, x, P);
+    return e[0] * P[0] + e[1] * P[1] + e[2] * P[2] + e[3] * P[3] + e[4] * P[4];
+}
+
+MB_HD float christoffel_weight(const Recon& R, float x) {
+    float P[5];
+    pis(R, x, P);
+    float K = 1.0f + R.h[0] * P[1] * P[1] + R.h[1] * P[2] * P[2] + R.h[2] * P[3] * P[3] + R.h[3] * P[4] * P[4];
+    float w = 1.0f / K;
+    return isfinite(w) ? w : 0.0f;
+}
+
+// Laguerre iteration towards the neighbouring root on one side.  For a
+// real-rooted polynomial the iterates move monotonically to the adjacent root
+// in the chosen direction, cubically near it.
+MB_HD float laguerre(const Recon& R, const float e[5], float x, float lo, float hi,
+                                          bool right) {
+#pragma unroll 1
+    for (int it = 0; it < LAG_ITERS; ++it) {
+        float p0 = 1.0f, p1 = x - R.al[0];
+        float d0 = 0.0f, d1 = 1.0f;
+        float s0 = 0.0f, s1 = 0.0f;
+        float f = e[0] + e[1] * p1, fp = e[1], fpp = 0.0f;
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            const float xa = x - R.al[k];
+            const float b = R.be[k - 1];
+            float p2 = fmaf(xa, p1, -b * p0);
+            float d2 = fmaf(xa, d1, fmaf(-b, d0, p1));
+            float s2 = fmaf(xa, s1, fmaf(-b, s0, 2.0f * d1));
+            f = fmaf(e[k + 1], p2, f);
+            fp = fmaf(e[k + 1], d2, fp);
+            fpp = fmaf(e[k + 1], s2, fpp);
+            p0 = p1; p1 = p2; d0 = d1; d1 = d2; s0 = s1; s1 = s2;
+        }
+        const float q = sqrtf(fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 0.0f));
+        const float sq = f >= 0.0f ? q : -q;
+        const float den = right ? fp - sq : fp + sq;
+        const float step = den != 0.0f ? 4.0f * f / den : 0.0f;
+        float xn = x - step;
+        xn = fminf(fmaxf(xn, lo), hi);
+        x = isfinite(xn) ? xn : x;
+    }
+    return x;
+}
+
+// tau(eta) = m0 ((1 - beta) L + beta U) = m0 (L + beta w0) at warped depth
+// y = 2 eta - 1 (Sec. 3.2, Eq. 8).
+MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
+    if (R.m0 <= 0.0f) return 0.0f;
+    const float y = (y_raw - R.c) * R.inv_s;
+    float P[5];
+    pis(R, y, P);
+    float e[5];
+    e[0] = 1.0f;
+    e[1] = R.h[0] * P[1];
+    e[2] = R.h[1] * P[2];
+    e[3] = R.h[2] * P[3];
+    e[4] = R.h[3] * P[4];
+    const float K = 1.0f + e[1] * P[1] + e[2] * P[2] + e[3] * P[3] + e[4] * P[4];
+    const float w0 = 1.0f / K;
+    const int j = (R.z[0] < y) + (R.z[1] < y) + (R.z[2] < y) + (R.z[3] < y);
+    // scale the kernel coefficients (roots are scale invariant) to keep f^2 finite
+    const float sc = 1.0f / (fabsf(e[0]) + fabsf(e[1]) + fabsf(e[2]) + fabsf(e[3]) + fabsf(e[4]));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) e[k] *= sc;
+    float L;
+    if (j == 0) {
+        L = 0.0f;
+    } else if (j == NQ) {
+        L = 1.0f - w0;
+    } else {
+        float acc = 0.0f;
+        // outer root: left of z_1 (j <= 2) or right of z_4 (j == 3)
+        const bool left = (j <= 2);
+        const float zb = left ? R.z[0] : R.z[3];
+        const float far = left ? zb - R.span : zb + R.span;
+        const float ff = kernel_poly(R, e, far);
+        const float fz = kernel_poly(R, e, zb);
+        if ((ff > 0.0f) != (fz > 0.0f)) {
+            float x = left ? laguerre(R, e, far, far, zb, true) : laguerre(R, e, far, zb, far, false);
+            acc += christoffel_weight(R, x);
+        }
+        if (j == 2) {
+            // interior root in (z_1, z_2), approached from z_2 (next to eta's interval)
+            float x = laguerre(R, e, R.z[1], R.z[0], R.z[1], false);
+            acc += christoffel_weight(R, x);
+        }
+        L = left ? acc : 1.0f - w0 - acc;
+    }
+    L = fminf(fmaxf(L, 0.0f), 1.0f - w0);
+    return R.m0 * fmaf(beta, w0, L);
+}
+
+// Modified Chebyshev algorithm (Gautschi) with monic Legendre reference
+// polynomials (a_k = 0, b_k = k^2 / (4k^2 - 1)): recurrence coefficients of
+// the biased, normalised moment measure from its Legendre moments.
+#ifndef MB_RECON_T
+#define MB_RECON_T double
+#endif
+MB_HD void reconstruct_pixel(const Params& p, const float I[NMOM], Recon& R) {
+    typedef MB_RECON_T real;
+    R.m0 = I[0];
+    if (!(I[0] >= p.m_min) || !isfinite(I[0])) {
+        R.m0 = 0.0f;
+        R.c = 0.0f; R.inv_s = 1.0f; R.span = 1.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { R.al[k] = 0.0f; R.be[k] = 0.25f; R.h[k] = 1.0f; R.z[k] = 0.0f; }
+        return;
+    }
+    // monic-Legendre modified moments of the normalised measure, biased towards U[-1,1]
+    const real cl[NMOM] = {1.0, 1.0, 2.0 / 3.0, 2.0 / 5.0, 8.0 / 35.0, 8.0 / 63.0, 16.0 / 231.0, 16.0 / 429.0,
+                           128.0 / 6435.0};
+    const real inv0 = real(1) / (real)I[0];
+    const real oma = real(1) - (real)p.bias_alpha;
+    real sg0[NMOM + 1], sg1[NMOM + 1], sg2[NMOM + 1];
+#pragma unroll
+    for (int l = 0; l < NMOM; ++l) {
+        sg1[l] = cl[l] * (real)I[l] * inv0 * oma;
+        sg0[l] = 0;
+    }
+    sg1[0] = 1;
+    sg1[NMOM] = 0;
+    sg0[NMOM] = 0;
+    real alr[4], ber[5];
+    ber[0] = 1;
+    alr[0] = sg1[1];
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) {
+#pragma unroll
+        for (int l = 0; l <= NMOM; ++l) sg2[l] = 0;
+#pragma unroll
+        for (int l = 1; l < NMOM; ++l) {
+            if (l >= k && l <= 8 - k) {
+                const real bl = (real)(l * l) / (real)(4 * l * l - 1);
+                sg2[l] = sg1[l + 1] - alr[k - 1] * sg1[l] - ber[k - 1] * sg0[l] + bl * sg1[l - 1];
+            }
+        }
+        ber[k] = sg2[k] / sg1[k - 1];
+        if (!(ber[k] > real(1e-30))) ber[k] = real(1e-30);
+        if (k < 4) alr[k] = sg2[k + 1] / sg2[k] - sg1[k] / sg1[k - 1];
+#pragma unroll
+        for (int l = 0; l <= NMOM; ++l) { sg0[l] = sg1[l]; sg1[l] = sg2[l]; }
+    }
+    // standardise: y' = (y - al_0) / sqrt(be_1); al' = (al - al_0)/s, be' = be / s^2, h' = 1/prod be'
+    const real sd = sqrt(ber[1]);
+    const real isd = real(1) / sd;
+    R.c = (float)alr[0];
+    R.inv_s = (float)isd;
+    R.span = (float)(OUTER_SPAN * isd);
+    float al[4], be[5];
+    be[0] = 1.0f;
+    real hk = 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) al[k] = (float)((alr[k] - alr[0]) * isd);
+#pragma unroll
+    for (int k = 1; k < 5; ++k) {
+        const real bs = ber[k] * isd * isd;
+        be[k] = (float)bs;
+        hk = hk / bs;
+        R.h[k - 1] = (float)hk;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { R.al[k] = al[k]; R.be[k] = be[k + 1]; }
+    // Gauss nodes: eigenvalues of the 4x4 Jacobi matrix by Sturm-count bisection
+    float sb[4];
+    sb[0] = 0.0f;
+    sb[1] = sqrtf(be[1]); sb[2] = sqrtf(be[2]); sb[3] = sqrtf(be[3]);
+    float lo = 1e30f, hi = -1e30f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float rad = (k > 0 ? sb[k] : 0.0f) + (k < 3 ? sb[k + 1] : 0.0f);
+        lo = fminf(lo, al[k] - rad);
+        hi = fmaxf(hi, al[k] + rad);
+    }
+    lo -= 1e-6f * (fabsf(lo) + 1.0f);
+    hi += 1e-6f * (fabsf(hi) + 1.0f);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float a = lo, b = hi;
+#pragma unroll 1
+        for (int it = 0; it < 40; ++it) {
+            const float x = 0.5f * (a + b);
+            int cnt = 0;
+            float d = al[0] - x;
+            cnt += d < 0.0f;
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                if (fabsf(d) < 1e-30f) d = -1e-30f;
+                d = (al[k] - x) - be[k] / d;
+                cnt += d < 0.0f;
+            }
+            if (cnt > e) b = x; else a = x;
+        }
+        R.z[e] = 0.5f * (a + b);
+    }
+}
+
+MB_HD Recon load_recon(const float* __restrict__ rc, int64_t npix, int64_t pix) {
+    Recon R;
+    R.m0 = rc[0 * npix + pix];
+    R.c = rc[1 * npix + pix];
+    R.inv_s = rc[2 * npix + pix];
+    R.span = rc[3 * npix + pix];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        R.al[k] = rc[(4 + k) * npix + pix];
+        R.be[k] = rc[(8 + k) * npix + pix];
+        R.h[k] = rc[(12 + k) * npix + pix];
+        R.z[k] = rc[(16 + k) * npix + pix];
+    }
+    return R;
+}
+
+MB_HD void store_recon(const Recon& R, float* __restrict__ rc, int64_t npix, int64_t pix) {
+    rc[0 * npix + pix] = R.m0;
+    rc[1 * npix + pix] = R.c;
+    rc[2 * npix + pix] = R.inv_s;
+    rc[3 * npix + pix] = R.span;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        rc[(4 + k) * npix + pix] = R.al[k];
+        rc[(8 + k) * npix + pix] = R.be[k];
+        rc[(12 + k) * npix + pix] = R.h[k];
+        rc[(16 + k) * npix + pix] = R.z[k];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Per-pair quadrature (Eq. 7 with App. B samples) and penalty (App. D).
+// NI > 0: compile-time number of intervals; NI == 0: runtime p.n_intervals.
+// Returns O_i; adds P_i to *pen.
+// ----------------------------------------------------------------------------
+template <int NI>
+MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, float* pen) {
+    constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
+    const int N = NI > 0 ? NI : p.n_intervals;
+    float t[NN], tau[NN];
+    const float ks = p.kappa * g.Sig;
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+        if (NI > 0 || j <= N) {
+            float tj = fminf(fmaxf(fmaf(ks, p.x_nodes[j], g.mu), p.t_near), p.t_far);
+            t[j] = tj;
+            float y = fmaf(2.0f, warp_only(p, tj), -1.0f);
+            tau[j] = optical_depth(R, p.beta, y);
+        }
+    }
+    const float inv2s2 = 0.5f / g.Sig2;
+    const float isq = 0.70710678118654752f / g.Sig;
+    const float tscale = g.what * g.Sig * 1.25331413731550025f;
+    float O = 0.0f, P = 0.0f;
+    float erf_prev = erff((t[0] - g.mu) * isq);
+#pragma unroll
+    for (int j = 0; j < NN - 1; ++j) {
+        if (NI > 0 || j < N) {
+            const float Delta = t[j + 1] - t[j];
+            const float dtau = fmaxf(tau[j + 1] - tau[j], 0.0f);
+            const float Tj = expf(-tau[j]);
+            const float dt0 = t[j] - g.mu;
+            const float sig = g.what * expf(-dt0 * dt0 * inv2s2);
+            const float ratio = dtau < 1e-6f ? fmaf(-0.5f, dtau, 1.0f) : -expm1f(-dtau) / dtau;
+            O = fmaf(Tj * ratio, sig * Delta, O);
+            const float erf_next = erff((t[j + 1] - g.mu) * isq);
+            const float tij = tscale * (erf_next - erf_prev);
+            const float v = fmaxf(tij - dtau, 0.0f);
+            P = fmaf(v, v, P);
+            erf_prev = erf_next;
+        }
+    }
+    *pen += P;
+    return O;
+}
+
+MB_HD int find_view(const ViewTable& vt, int64_t tile) {
+    int v = 0;
+    for (int k = 1; k < vt.n_views; ++k)
+        if (tile >= vt.v[k].tile_base) v = k;
+    return v;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) { atomicMin(status, code); }
+
+// host-side count of kernel launches issued by the library (for reporting)
+void count_launch(int n = 1);
+
+}  // namespace mb

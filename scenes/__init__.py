@@ -84,7 +84,8 @@ def look_at(eye, target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), fov_deg=60.0,
     V[:3, :3] = R
     V[:3, 3] = t
     fy = (height / 2.0) / math.tan(math.radians(fov_deg) / 2.0)
-    return Camera(V.astype(np.float32), float(fy), float(fy), width / 2.0, height / 2.0,
+    f32 = lambda x: float(np.float32(x))     # the C ABI takes float32 intrinsics
+    return Camera(V.astype(np.float32), f32(fy), f32(fy), f32(width / 2.0), f32(height / 2.0),
                   int(width), int(height), eye.copy())
 
 

@@ -1,0 +1,81 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads, and
+exports every entry point declared in include/mb3dgs.h; host-only calls
+validate arguments and size workspaces."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "mb3dgs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mb3dgs_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_11800_gb300 import _binding as B
+    return B.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2512_11800_gb300 import _binding as B
+    syms = declared_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(B.EXPORTS) == syms
+
+
+def test_config_defaults_and_status_strings(lib):
+    from paper_2512_11800_gb300 import _binding as B
+    c = B.Config()
+    assert lib.mb3dgs_config_default(C.byref(c)) == 0
+    assert c.n == 4 and c.n_intervals == 3 and abs(c.beta - 0.25) < 1e-7 and abs(c.kappa - 3) < 1e-7
+    assert abs(c.conf_c - 0.01) < 1e-8 and abs(c.warp_lambda + 1.5) < 1e-7 and abs(c.bias_alpha - 1e-3) < 1e-9
+    for code in [0, -1, -2, -3, -4, -5, -6, -7]:
+        assert lib.mb3dgs_status_string(code).decode() == B.STATUS[code]
+
+
+def _cam(W=1920, H=1080):
+    import scenes
+    from paper_2512_11800_gb300 import to_camera
+    return to_camera(scenes.look_at((0, 0, -3), width=W, height=H))
+
+
+def test_workspace_size_and_validation(lib):
+    from paper_2512_11800_gb300 import _binding as B
+    c = B.Config()
+    lib.mb3dgs_config_default(C.byref(c))
+    cam = _cam()
+    n = C.c_size_t(0)
+    assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 1000, 0, C.byref(n)) == 0
+    a = n.value
+    assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 1000, 1 << 20, C.byref(n)) == 0
+    assert n.value >= a + 16 * (1 << 20)            # four 32-bit pair arrays
+    assert lib.mb3dgs_num_tiles(C.byref(cam), 1) == 120 * 68
+    bad = B.Config()
+    lib.mb3dgs_config_default(C.byref(bad))
+    bad.n = 3
+    assert lib.mb3dgs_workspace_size(C.byref(bad), C.byref(cam), 1, 10, 0, C.byref(n)) == -6
+    bad.n, bad.n_intervals = 4, 0
+    assert lib.mb3dgs_workspace_size(C.byref(bad), C.byref(cam), 1, 10, 0, C.byref(n)) == -6
+    bad.n_intervals, bad.conf_c = 3, 1.5
+    assert lib.mb3dgs_workspace_size(C.byref(bad), C.byref(cam), 1, 10, 0, C.byref(n)) == -1
+    assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 0, 10, 0, C.byref(n)) == -1
+    assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 10, 1 << 31, C.byref(n)) == -1
+    cam.width = 0
+    assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 10, 0, C.byref(n)) == -1
+    # null workspace with a non-empty layout is rejected before any CUDA call
+    g = B.Gaussians()
+    assert lib.mb3dgs_preprocess(C.byref(c), C.byref(g), C.byref(_cam()), 1, None, 0, 0, None) == -1
+
+
+def test_multiview_tiles(lib):
+    from paper_2512_11800_gb300 import _binding as B
+    cams = (B.Camera * 3)(_cam(640, 360), _cam(1280, 720), _cam(1920, 1080))
+    assert lib.mb3dgs_num_tiles(cams, 3) == 40 * 23 + 80 * 45 + 120 * 68
