@@ -353,36 +353,50 @@ MB_HD void reconstruct_pixel(const Params& p, const float I[NMOM], Recon& R) {
     const real cl[NMOM] = {1.0, 1.0, 2.0 / 3.0, 2.0 / 5.0, 8.0 / 35.0, 8.0 / 63.0, 16.0 / 231.0, 16.0 / 429.0,
                            128.0 / 6435.0};
     const real inv0 = real(1) / (real)I[0];
-    const real oma = real(1) - (real)p.bias_alpha;
-    real sg0[NMOM + 1], sg1[NMOM + 1], sg2[NMOM + 1];
-#pragma unroll
-    for (int l = 0; l < NMOM; ++l) {
-        sg1[l] = cl[l] * (real)I[l] * inv0 * oma;
-        sg0[l] = 0;
-    }
-    sg1[0] = 1;
-    sg1[NMOM] = 0;
-    sg0[NMOM] = 0;
     real alr[4], ber[5];
-    ber[0] = 1;
-    alr[0] = sg1[1];
+    // Moments rounded to 16-bit storage can leave the feasible set (a
+    // non-positive be_k); the bias towards U[-1,1] is then raised for this
+    // pixel (x4 per attempt) until the recurrence is positive definite.  With
+    // FP32 storage and the default bias the first attempt always succeeds.
+    real alpha = (real)p.bias_alpha;
+#pragma unroll 1
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        const real oma = real(1) - alpha;
+        real sg0[NMOM + 1], sg1[NMOM + 1], sg2[NMOM + 1];
 #pragma unroll
-    for (int k = 1; k <= 4; ++k) {
-#pragma unroll
-        for (int l = 0; l <= NMOM; ++l) sg2[l] = 0;
-#pragma unroll
-        for (int l = 1; l < NMOM; ++l) {
-            if (l >= k && l <= 8 - k) {
-                const real bl = (real)(l * l) / (real)(4 * l * l - 1);
-                sg2[l] = sg1[l + 1] - alr[k - 1] * sg1[l] - ber[k - 1] * sg0[l] + bl * sg1[l - 1];
-            }
+        for (int l = 0; l < NMOM; ++l) {
+            sg1[l] = cl[l] * (real)I[l] * inv0 * oma;
+            sg0[l] = 0;
         }
-        ber[k] = sg2[k] / sg1[k - 1];
-        if (!(ber[k] > real(1e-30))) ber[k] = real(1e-30);
-        if (k < 4) alr[k] = sg2[k + 1] / sg2[k] - sg1[k] / sg1[k - 1];
+        sg1[0] = 1;
+        sg1[NMOM] = 0;
+        sg0[NMOM] = 0;
+        ber[0] = 1;
+        alr[0] = sg1[1];
+        bool ok = true;
 #pragma unroll
-        for (int l = 0; l <= NMOM; ++l) { sg0[l] = sg1[l]; sg1[l] = sg2[l]; }
+        for (int k = 1; k <= 4; ++k) {
+#pragma unroll
+            for (int l = 0; l <= NMOM; ++l) sg2[l] = 0;
+#pragma unroll
+            for (int l = 1; l < NMOM; ++l) {
+                if (l >= k && l <= 8 - k) {
+                    const real bl = (real)(l * l) / (real)(4 * l * l - 1);
+                    sg2[l] = sg1[l + 1] - alr[k - 1] * sg1[l] - ber[k - 1] * sg0[l] + bl * sg1[l - 1];
+                }
+            }
+            ber[k] = sg2[k] / sg1[k - 1];
+            if (!(ber[k] > real(1e-12)) || !(ber[k] < real(1e12))) ok = false;
+            if (k < 4) alr[k] = sg2[k + 1] / sg2[k] - sg1[k] / sg1[k - 1];
+#pragma unroll
+            for (int l = 0; l <= NMOM; ++l) { sg0[l] = sg1[l]; sg1[l] = sg2[l]; }
+        }
+        if (ok || alpha >= real(0.5)) break;
+        alpha = alpha * 4 < real(0.5) ? alpha * 4 : real(0.5);
     }
+#pragma unroll
+    for (int k = 1; k <= 4; ++k)
+        if (!(ber[k] > real(1e-12))) ber[k] = real(1e-12);
     // standardise: y' = (y - al_0) / sqrt(be_1); al' = (al - al_0)/s, be' = be / s^2, h' = 1/prod be'
     const real sd = sqrt(ber[1]);
     const real isd = real(1) / sd;
