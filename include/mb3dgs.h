@@ -181,6 +181,30 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
                     int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
                     const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream);
 
+/* Size of the fixed device workspace used by mb3dgs_render_noalloc. */
+#define MB3DGS_NOALLOC_WORKSPACE_BYTES (64u << 20)
+
+/* mb3dgs_render without any device allocation, for callers that cannot call
+ * cudaMalloc or hand the library memory from an allocator (plug-ins in a host
+ * that owns all device memory, loops that must not allocate).  The paper has
+ * no counterpart; this is a deployment convenience.
+ * The workspace is a static device array of MB3DGS_NOALLOC_WORKSPACE_BYTES
+ * (64 MiB) that every GPU loading the library reserves until process exit.
+ * Inputs and outputs are the caller's, as in mb3dgs_render; d_status (one
+ * int32, device) receives the call's status word (MB3DGS_OK or e.g.
+ * MB3DGS_ERR_CAPACITY when the frame has more (tile, Gaussian) pairs than fit
+ * in the space left after the per-Gaussian and per-pixel buffers).
+ * Returns MB3DGS_ERR_WORKSPACE_TOO_SMALL, before launching anything, when the
+ * Gaussians, views and pixels alone need more than the fixed size.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call uses the same array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the caller.
+ * Allocates nothing (no cudaMalloc / cudaFree). */
+int mb3dgs_render_noalloc(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
+                          int n_views, float* d_rgb, float* d_T_final, float* d_penalty, int32_t* d_status,
+                          mb3dgs_stream_t stream);
+
 /* Synchronises the stream and reads the workspace status word (an MB3DGS_*
  * code) and the number of (tile, Gaussian) pairs of the last binning. */
 int mb3dgs_get_status(const void* ws, size_t ws_bytes, int* status, int64_t* n_pairs, mb3dgs_stream_t stream);

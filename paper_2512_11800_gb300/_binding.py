@@ -37,7 +37,7 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace too 
 
 EXPORTS = ["mb3dgs_status_string", "mb3dgs_last_cuda_error", "mb3dgs_config_default", "mb3dgs_workspace_size", "mb3dgs_preprocess",
            "mb3dgs_bin_tiles", "mb3dgs_accumulate_moments", "mb3dgs_reconstruct_transmittance", "mb3dgs_shade",
-           "mb3dgs_render", "mb3dgs_backward", "mb3dgs_get_status", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count"]
+           "mb3dgs_render", "mb3dgs_render_noalloc", "mb3dgs_backward", "mb3dgs_get_status", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count"]
 
 _lib = None
 
@@ -57,6 +57,7 @@ def _declare(lib):
         "mb3dgs_reconstruct_transmittance": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, C.c_int, vp, vp]),
         "mb3dgs_shade": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp, vp]),
         "mb3dgs_render": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, vp, vp]),
+        "mb3dgs_render_noalloc": (C.c_int, [cfg, gs, cam, C.c_int, vp, vp, vp, vp, vp]),
         "mb3dgs_backward": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, gg, vp]),
         "mb3dgs_get_status": (C.c_int, [vp, sz, P(C.c_int), P(i64), vp]),
         "mb3dgs_debug_tile_lists": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp, vp]),

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -395,3 +396,75 @@ int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams,
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------
+// Render without any device allocation by the caller or the library.
+//
+// Some callers cannot call cudaMalloc (or cannot hand the library a workspace
+// from an allocator): code running where allocation is forbidden or unsafe,
+// such as plug-ins inside a host that owns all device memory, real-time loops
+// that must not allocate, or code paths that run while another component holds
+// the allocator.  For them mb3dgs_render_noalloc uses a workspace that is a
+// file-scope static device array of fixed size, reserved on every GPU that
+// loads this library until the process exits.
+// ----------------------------------------------------------------------------
+namespace mb {
+static __device__ __align__(256) unsigned char g_noalloc_ws[MB3DGS_NOALLOC_WORKSPACE_BYTES];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[256] = {};
+
+// Device address of the static workspace for the current device; looked up once
+// per device (the array's host-side name is only a stand-in, not a device address).
+static int noalloc_workspace(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return MB3DGS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
+        if (e != cudaSuccess || p == nullptr) {
+            g_last_cuda_error = cudaGetErrorString(e);
+            return MB3DGS_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MB3DGS_OK;
+}
+}  // namespace mb
+
+extern "C" int mb3dgs_render_noalloc(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
+                                     int n_views, float* d_rgb, float* d_T_final, float* d_penalty, int32_t* d_status,
+                                     mb3dgs_stream_t stream) {
+    if (!g || !d_rgb || !d_T_final || !d_status) return MB3DGS_ERR_INVALID_ARG;
+    int rc = check_cfg(cfg);
+    if (rc) return rc;
+    ViewTable vt;
+    int64_t npix, nt;
+    rc = make_views(cams, n_views, vt, npix, nt);
+    if (rc) return rc;
+    const size_t cap_bytes = (size_t)MB3DGS_NOALLOC_WORKSPACE_BYTES;
+    Layout L;
+    rc = make_layout(cfg, vt, npix, nt, g->P, 0, L);
+    if (rc) return rc;
+    if (L.total > cap_bytes) return MB3DGS_ERR_WORKSPACE_TOO_SMALL;   // P / pixels beyond the fixed maximum
+    // largest pair capacity whose layout still fits the static array
+    int64_t lo = 0, hi = (int64_t(1) << 31) - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        Layout t;
+        if (make_layout(cfg, vt, npix, nt, g->P, mid, t) == MB3DGS_OK && t.total <= cap_bytes) lo = mid;
+        else hi = mid - 1;
+    }
+    void* ws = nullptr;
+    rc = noalloc_workspace(&ws);
+    if (rc) return rc;
+    rc = mb3dgs_render(cfg, g, cams, n_views, ws, cap_bytes, lo, d_rgb, d_T_final, d_penalty, stream);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the status word (first int of the workspace header) goes to the caller's output
+    if (cudaMemcpyAsync(d_status, ws, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return MB3DGS_ERR_CUDA;
+    return cuda_ok();
+}
