@@ -20,7 +20,7 @@ constexpr int NQ = 4;                 // n: roots of the kernel polynomial
 constexpr int REC = 32;               // floats per (view, Gaussian) record
 constexpr int RECON = 20;             // floats per pixel of reconstruction state
 constexpr int MAX_NODES = 9;          // N+1 <= 9 sample points
-constexpr int LAG_ITERS = 6;          // Laguerre iterations per root
+constexpr int LAG_ITERS = 4;          // Laguerre iterations per root
 constexpr double OUTER_SPAN = 8.0;   // outer-root search span beyond the Gauss nodes (y units)
 
 // record field offsets (floats)
@@ -103,6 +103,15 @@ struct Layout {
 __host__ __device__ inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 #define MB_HD __host__ __device__ __forceinline__
+
+// approximate division (2 ulp) where the quotient feeds an iteration or a weight
+MB_HD float fdiv_(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
 
 MB_HD float rsqrt_(float x) {
 #ifdef __CUDA_ARCH__
@@ -247,7 +256,7 @@ MB_HD float christoffel_weight(const Recon& R, float x) {
     float P[5];
     pis(R, x, P);
     float K = 1.0f + R.h[0] * P[1] * P[1] + R.h[1] * P[2] * P[2] + R.h[2] * P[3] * P[3] + R.h[3] * P[4] * P[4];
-    float w = 1.0f / K;
+    float w = fdiv_(1.0f, K);
     return isfinite(w) ? w : 0.0f;
 }
 
@@ -277,7 +286,7 @@ MB_HD float laguerre(const Recon& R, const float e[5], float x, float lo, float 
         const float q = sqrtf(fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 0.0f));
         const float sq = f >= 0.0f ? q : -q;
         const float den = right ? fp - sq : fp + sq;
-        const float step = den != 0.0f ? 4.0f * f / den : 0.0f;
+        const float step = den != 0.0f ? fdiv_(4.0f * f, den) : 0.0f;
         float xn = x - step;
         xn = fminf(fmaxf(xn, lo), hi);
         x = isfinite(xn) ? xn : x;
@@ -299,10 +308,10 @@ MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
     e[3] = R.h[2] * P[3];
     e[4] = R.h[3] * P[4];
     const float K = 1.0f + e[1] * P[1] + e[2] * P[2] + e[3] * P[3] + e[4] * P[4];
-    const float w0 = 1.0f / K;
+    const float w0 = fdiv_(1.0f, K);
     const int j = (R.z[0] < y) + (R.z[1] < y) + (R.z[2] < y) + (R.z[3] < y);
     // scale the kernel coefficients (roots are scale invariant) to keep f^2 finite
-    const float sc = 1.0f / (fabsf(e[0]) + fabsf(e[1]) + fabsf(e[2]) + fabsf(e[3]) + fabsf(e[4]));
+    const float sc = fdiv_(1.0f, fabsf(e[0]) + fabsf(e[1]) + fabsf(e[2]) + fabsf(e[3]) + fabsf(e[4]));
 #pragma unroll
     for (int k = 0; k < 5; ++k) e[k] *= sc;
     float L;
@@ -402,7 +411,7 @@ MB_HD void reconstruct_pixel(const Params& p, const float I[NMOM], Recon& R) {
     const real isd = real(1) / sd;
     R.c = (float)alr[0];
     R.inv_s = (float)isd;
-    R.span = (float)(OUTER_SPAN * isd);
+    const real span_max = OUTER_SPAN * isd;
     float al[4], be[5];
     be[0] = 1.0f;
     real hk = 1;
@@ -417,6 +426,14 @@ MB_HD void reconstruct_pixel(const Params& p, const float I[NMOM], Recon& R) {
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) { R.al[k] = al[k]; R.be[k] = be[k + 1]; }
+    // Beyond distance d of the outermost Gauss node a root's Christoffel weight is
+    // below 1/(h_4 d^8) (K(x,x) >= h_4 pi_4(x)^2 >= h_4 d^8): search only up to
+    // the d where that bound reaches 1e-7, at most 8 warped-depth units.
+    {
+        real d = pow((real)R.h[3] * real(1e-7), real(-0.125));
+        d = d < real(1) ? real(1) : d;
+        R.span = (float)(d < span_max ? d : span_max);
+    }
     // Gauss nodes: eigenvalues of the 4x4 Jacobi matrix by Sturm-count bisection
     float sb[4];
     sb[0] = 0.0f;

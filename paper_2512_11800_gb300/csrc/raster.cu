@@ -62,8 +62,11 @@ __device__ __forceinline__ PixelCtx pixel_ctx(const ViewTable& vt, const int2* _
     const ViewDesc& V = vt.v[c.v];
     const int lt = (int)(tile - V.tile_base);
     const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-    c.px = tx * TILE + (threadIdx.x % TILE);
-    c.py = ty * TILE + (threadIdx.x / TILE);
+    // each warp covers an 8x4 block of the tile (fewer partially covered warps
+    // than 16x2 rows for rectangle-shaped footprints)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    c.px = tx * TILE + (warp & 1) * 8 + (lane & 7);
+    c.py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
     c.inside = c.px < V.width && c.py < V.height;
     c.pix = V.pixel_base + (int64_t)c.py * V.width + c.px;
     const float ux = ((float)c.px + 0.5f - V.cx) / V.fx;
@@ -192,7 +195,7 @@ __global__ void k_reconstruct(Params p, const void* __restrict__ moments, int64_
 
 // ---------------------------------------------------------------- quadrature pass
 template <int NI>
-__global__ void __launch_bounds__(TPB, 2) k_shade(Params p, ViewTable vt, const float* __restrict__ rec,
+__global__ void __launch_bounds__(TPB, 3) k_shade(Params p, ViewTable vt, const float* __restrict__ rec,
                                                const int32_t* __restrict__ ids, const int2* __restrict__ ranges,
                                                int64_t P, int64_t npix, const StatusWordsR* sw,
                                                const float* __restrict__ recon, const void* __restrict__ moments,
