@@ -158,6 +158,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forward-only", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -186,7 +187,13 @@ def main():
     wsp, wsn = C.c_void_p(ws.data_ptr()), ws.numel()
     rgb, T, pen = out["rgb"], out["T"], out["penalty"]
 
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
+    dL_drgb = torch.empty_like(rgb)
+    grads = {k: torch.empty_like(getattr(g, k)) for k in ["means", "scales", "quats", "weights", "sh"]}
+    gg = B.GaussianGrads()
+    gg.means, gg.scales, gg.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
+    gg.weights, gg.sh = grads["weights"].data_ptr(), grads["sh"].data_ptr()
+    with_bwd = not args.forward_only
 
     def step(record=None):
         if record is not None:
@@ -205,12 +212,19 @@ def main():
                                  C.c_void_p(T.data_ptr()), C.c_void_p(pen.data_ptr()), s), "shade")
         if record is not None:
             record[4].record(stream)
+        if with_bwd:
+            # L2 loss against the random target image (the loss itself is the caller's)
+            torch.sub(rgb, target, out=dL_drgb).mul_(2.0 / rgb.numel())
+            B.check(lib.mb3dgs_backward(cfg, C.byref(gc), arr, nv, wsp, wsn, cap, C.c_void_p(dL_drgb.data_ptr()),
+                                        None, C.byref(gg), s), "backward")
+        if record is not None:
+            record[5].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     # per-stage times (device, CUDA events on the launching stream)
-    stage = {"preprocess+bin": [], "moments": [], "reconstruct": [], "shade": []}
+    stage = {"preprocess+bin": [], "moments": [], "reconstruct": [], "shade": [], "backward": []}
     clocks = ClockSampler()
     if dist:
         dist.barrier()
@@ -219,7 +233,7 @@ def main():
     l0 = lib.mb3dgs_launch_count()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     t_start.record(stream)
     for k in range(args.steps):
         step(evs[k])
@@ -233,6 +247,7 @@ def main():
         stage["moments"].append(e[1].elapsed_time(e[2]))
         stage["reconstruct"].append(e[2].elapsed_time(e[3]))
         stage["shade"].append(e[3].elapsed_time(e[4]))
+        stage["backward"].append(e[4].elapsed_time(e[5]))
     stage_ms = {k: statistics.median(v) for k, v in stage.items()}
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -255,12 +270,18 @@ def main():
     d2h = rgb_host.numel() * 4
     g2 = GaussianTensors(dev_in["means"], dev_in["scales"], dev_in["quats"], dev_in["weights"], dev_in["sh"],
                          sc.sh_degree)
-    outbuf = dict(rgb=torch.empty(npix, 3, device=dev), T=torch.empty(npix, device=dev), penalty=None)
+    outbuf = dict(rgb=torch.empty(npix, 3, device=dev), T=torch.empty(npix, device=dev),
+                  penalty=torch.empty(npix, device=dev))
+
+    grads2 = {k: torch.empty_like(v) for k, v in dev_in.items()}
 
     def e2e_step():
         for k in host:
             dev_in[k].copy_(host[k], non_blocking=True)
-        o = R.render(g2, cam, capacity=cap, out=outbuf, penalty=False)
+        o = R.render(g2, cam, capacity=cap, out=outbuf, penalty=True)
+        if with_bwd:
+            dl = (o["rgb"] - target).mul_(2.0 / o["rgb"].numel())
+            R.backward(g2, cam, cap, dl, None, grads=grads2)
         rgb_host.copy_(o["rgb"], non_blocking=True)
 
     for _ in range(2):
@@ -283,6 +304,7 @@ def main():
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at max SM clock
+    fwd_ms = sum(stage_ms[k] for k in ["preprocess+bin", "moments", "reconstruct", "shade"])
     flops = pairs * shade_flops_per_pair(3)
     achieved = flops / (stage_ms["shade"] * 1e-3) / 1e12
     line = dict(
@@ -291,8 +313,10 @@ def main():
         unit="Mpixel/s",
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        fwd_mpix_s=world * npix / (fwd_ms * 1e-3) / 1e6,
         config=dict(workload=WORKLOAD, gaussians=g.P, width=cam.width, height=cam.height, sh_degree=3,
-                    n_moments=9, n_intervals=3, pass_="forward", l2="inputs larger than L2 (236 MB Gaussian "
+                    n_moments=9, n_intervals=3, pass_="forward+backward (L2 loss vs random target)" if with_bwd
+                    else "forward", l2="inputs larger than L2 (236 MB Gaussian "
                     "parameters + 128 MB records per step)", parallelism="replicas" if world > 1 else "1 GPU"),
         stage_ms=stage_ms,
         pairs=pairs, tile_pairs=npairs_tiles, status=st,

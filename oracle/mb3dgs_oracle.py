@@ -192,9 +192,14 @@ def gaussian_moments(mu, Sigma, w_hat, cfg: OracleConfig):
     m1 = g m0 + g' w Sigma^2 e^{-b_n^2}
     mk = g m_{k-1} + g'^2 Sigma^2 (k-1) m_{k-2} + g' w Sigma^2 u_n^{k-1} e^{-b_n^2}
     (the boundary term enters with "+": it is -B_i(k) with B_i(k) negative,
-    App. C; u_n = g(mu) + g'(mu)(t_n - mu) as in the derivation)."""
-    g, dg = warp(mu, cfg)
+    App. C; u_n = g(mu) + g'(mu)(t_n - mu) as in the derivation).
+    g-hat is defined on [t_n, t_f] only: for a Gaussian whose mean lies before
+    the near bound (mu < t_n) the linearisation point is t_n (reading), i.e.
+    u_t = g(c) + g'(c)(t - c) with c = max(mu, t_n), written a + s (t - mu)."""
     tn = cfg.t_near
+    c = torch.clamp(mu, min=tn)
+    gc, dg = warp(c, cfg)
+    g = gc + dg * (mu - c)
     bn = (tn - mu) / (math.sqrt(2.0) * Sigma)
     en = torch.exp(-bn * bn)
     un = g + dg * (tn - mu)
@@ -259,7 +264,13 @@ def canonical_representation(b, eta, n):
     roots = r0 - p / dp.detach()
     x = torch.cat([eta[..., None], roots], -1)
     V = x[..., None, :] ** powers[:, None]                     # V[k, i] = x_i^k
-    wts = torch.linalg.solve(V, b[..., :n + 1, None])[..., 0]
+    # Column equilibration of the Vandermonde system: column i is divided by
+    # max(1, |x_i|)^n and the solution multiplied back. The solved system is
+    # unchanged, but a root far outside [0, 1] (a kernel polynomial whose
+    # leading coefficient passes through zero) no longer leaves the system
+    # ill-conditioned and smearing rounding error over the other weights.
+    s = torch.clamp(x.detach().abs(), min=1.0) ** n
+    wts = torch.linalg.solve(V / s[..., None, :], b[..., :n + 1, None])[..., 0] / s
     return x, wts
 
 
@@ -559,3 +570,35 @@ def exact_optical_depth(mu, Sigma, w_hat, t, cfg: OracleConfig):
     b = (cfg.t_near - mu[..., None, :]) / s2
     term = w_hat[..., None, :] * Sigma[..., None, :] * math.sqrt(math.pi / 2.0) * (torch.special.erf(a) - torch.special.erf(b))
     return term.sum(-1)
+
+
+# ----------------------------------------------------------------------------
+# oracle gradient: autograd through render (roots differentiated implicitly)
+# ----------------------------------------------------------------------------
+def render_grad(scene, cam, cfg: OracleConfig = None, dL_drgb=None, dL_dP=None, region=None):
+    """Gradient of sum(dL_drgb * rgb) + sum(dL_dP * P) over the region with
+    respect to (means, scales, quats, weights, sh); proxy rectangles and
+    culling are constants (computed without gradient)."""
+    cfg = cfg or OracleConfig()
+    params = [torch.tensor(np.asarray(a, dtype=np.float64), requires_grad=True)
+              for a in (scene.means, scene.scales, scene.quats, scene.weights, scene.sh)]
+    out = render(scene, cam, cfg, region=region, params=tuple(params))
+    loss = (out["rgb"] * torch.as_tensor(np.asarray(dL_drgb), dtype=DT)).sum()
+    if dL_dP is not None:
+        loss = loss + (out["P"] * torch.as_tensor(np.asarray(dL_dP), dtype=DT)).sum()
+    grads = torch.autograd.grad(loss, params, allow_unused=True)
+    names = ["means", "scales", "quats", "weights", "sh"]
+    res = {n: (g.detach().numpy() if g is not None else np.zeros(p.shape)) for n, g, p in zip(names, grads, params)}
+    res["loss"] = float(loss.detach())
+    res["out"] = out
+    return res
+
+
+def render_loss(scene, cam, cfg, dL_drgb, dL_dP=None, region=None):
+    """The scalar loss of render_grad without gradient (for finite differences)."""
+    with torch.no_grad():
+        out = render(scene, cam, cfg, region=region)
+        loss = (out["rgb"] * torch.as_tensor(np.asarray(dL_drgb), dtype=DT)).sum()
+        if dL_dP is not None:
+            loss = loss + (out["P"] * torch.as_tensor(np.asarray(dL_dP), dtype=DT)).sum()
+    return float(loss), out["pre"].rect

@@ -16,7 +16,7 @@ import torch
 
 from . import _binding as B
 
-__all__ = ["RasterConfig", "GaussianTensors", "Rasterizer", "to_camera", "load_library"]
+__all__ = ["RasterConfig", "GaussianTensors", "Rasterizer", "to_camera", "load_library", "render"]
 
 
 def load_library():
@@ -219,3 +219,46 @@ class Rasterizer:
                                                  _ptr(ranges), _ptr(rects), s), "debug_tile_lists")
         return dict(rgb=rgb, T=T, penalty=pen, moments=mom, T_eta=Tq, ids=ids[:capacity], ranges=ranges, rects=rects,
                     capacity=int(capacity))
+
+    def backward(self, g: GaussianTensors, cams, capacity, dL_drgb, dL_dP=None, stream=None, grads=None):
+        """Adjoint of the last ``render`` (same Gaussians, cameras and capacity):
+        gradients of sum(dL_drgb * rgb) + sum(dL_dP * penalty) with respect to
+        the Gaussian parameters (mb3dgs_backward)."""
+        arr, nv = self.cameras(cams)
+        ws = self._ws
+        if grads is None:
+            grads = {k: torch.empty_like(getattr(g, k)) for k in ["means", "scales", "quats", "weights", "sh"]}
+        gc = g.to_c()
+        gg = B.GaussianGrads()
+        gg.means, gg.scales, gg.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
+        gg.weights, gg.sh = grads["weights"].data_ptr(), grads["sh"].data_ptr()
+        dL_drgb = dL_drgb.contiguous().float()
+        if dL_dP is not None:
+            dL_dP = dL_dP.contiguous().float()
+        B.check(self.lib.mb3dgs_backward(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(),
+                                         int(capacity), _ptr(dL_drgb), _ptr(dL_dP), C.byref(gg), _stream(stream)),
+                "backward")
+        return grads
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rast, cams, sh_degree, means, scales, quats, weights, sh):
+        g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), weights.contiguous(),
+                            sh.contiguous(), sh_degree)
+        out = rast.render(g, cams)
+        ctx.rast, ctx.cams, ctx.g, ctx.capacity = rast, cams, g, out["capacity"]
+        return out["rgb"], out["T"], out["penalty"]
+
+    @staticmethod
+    def backward(ctx, d_rgb, d_T, d_pen):
+        # the transmittance output e^{-m0} is not differentiated (treated as a diagnostic)
+        grads = ctx.rast.backward(ctx.g, ctx.cams, ctx.capacity, d_rgb, d_pen)
+        return None, None, None, grads["means"], grads["scales"], grads["quats"], grads["weights"], grads["sh"]
+
+
+def render(rast: "Rasterizer", cams, means, scales, quats, weights, sh, sh_degree):
+    """Differentiable render: returns (rgb [Npix,3], T [Npix], penalty [Npix]).
+    Backward runs the adjoint passes of mb3dgs_backward (the workspace of this
+    forward must not be reused before backward)."""
+    return _RenderFn.apply(rast, cams, sh_degree, means, scales, quats, weights, sh)

@@ -124,7 +124,7 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.recon = take(sizeof(float) * RECON * (size_t)npix);
     L.saved = take(sizeof(float) * 4 * (size_t)npix);
     L.dm = take(sizeof(float) * NMOM * (size_t)npix);
-    L.grec = take(sizeof(float) * 16 * (size_t)L.VP);
+    L.grec = take(sizeof(float) * 28 * (size_t)L.VP);
     L.total = o;
     return MB3DGS_OK;
 }
@@ -143,6 +143,14 @@ static void make_params(const mb3dgs_config* c, Params& p) {
     p.G1 = (float)G1;
     p.G0 = (float)((-a / lam - fn) / (ff - fn));
     p.G2 = (float)(G1 * lam * 2.0 / a);
+    p.G3 = (float)(G1 * lam * 2.0 / a * (lam - 1.0) * 2.0 / a);
+    {
+        const double r1 = std::sqrt(5.0 - 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+        const double r2 = std::sqrt(5.0 + 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+        const double w1 = (322.0 + 13.0 * std::sqrt(70.0)) / 900.0, w2 = (322.0 - 13.0 * std::sqrt(70.0)) / 900.0;
+        const double ys[5] = {-r2, -r1, 0.0, r1, r2}, ws[5] = {w2, w1, 128.0 / 225.0, w1, w2};
+        for (int m = 0; m < 5; ++m) { p.gl_y[m] = (float)ys[m]; p.gl_w[m] = (float)(0.5 * ws[m]); }
+    }
     p.two_over_a = (float)(2.0 / a);
     p.lam_is_m15 = c->warp_lambda == -1.5f;
     const int N = c->n_intervals;

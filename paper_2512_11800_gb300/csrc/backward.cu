@@ -1,9 +1,394 @@
-// Adjoint of the moment rasterizer (filled in by the backward implementation).
-#include "common.cuh"
+// Backward kernels: adjoint-moment pass, gradient pass, preprocessing adjoint.
+// The rescaling derivative (Eq. 15) is folded into both passes as in the
+// paper's two-pass adjoint (Sec. 3.3, App. C "Adjoint rendering"); the proxy
+// rectangles and the culling are constants.  Per-Gaussian sums over pixels use
+// a warp reduction, one shared-memory accumulator per staged record and one
+// global atomicAdd per (tile, record, field).
+#include "backward.cuh"
+#include "preprocess.cuh"
 
 namespace mb {
-int launch_backward(const Params&, const ViewTable&, const Layout&, char*, const mb3dgs_gaussians&, const float*,
-                    const float*, const mb3dgs_gaussian_grads&, cudaStream_t) {
-    return MB3DGS_ERR_UNSUPPORTED;
+
+struct StatusWordsB {
+    int status;
+    int pad;
+    long long n_total;
+    long long n_valid;
+    unsigned long long nonfinite;
+};
+
+__device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
+
+__device__ __forceinline__ int stage_batch_b(float* s_rec, const float* __restrict__ rec,
+                                             const int32_t* __restrict__ ids, int64_t rec_base, int start, int end,
+                                             int b) {
+    const int first = start + b * TPB;
+    const int nb = min(TPB, end - first);
+#pragma unroll
+    for (int j = 0; j < REC / 4; ++j) {
+        const int lin = j * TPB + threadIdx.x;
+        const int rr = lin >> 3, cc = lin & 7;
+        if (rr < nb) cp_async16b(s_rec + rr * REC + cc * 4, rec + (rec_base + ids[first + rr]) * REC + cc * 4);
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    __syncthreads();
+    return nb;
+}
+
+struct BwdPixel {
+    int v, px, py;
+    bool inside;
+    int64_t pix;
+    float rlen, r2;
+    int start, end;
+    int64_t rec_base;
+};
+
+__device__ __forceinline__ BwdPixel bwd_pixel(const ViewTable& vt, const int2* __restrict__ ranges, int64_t P,
+                                              int64_t tile) {
+    BwdPixel c;
+    c.v = find_view(vt, tile);
+    const ViewDesc& V = vt.v[c.v];
+    const int lt = (int)(tile - V.tile_base);
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    c.px = tx * TILE + (warp & 1) * 8 + (lane & 7);
+    c.py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
+    c.inside = c.px < V.width && c.py < V.height;
+    c.pix = V.pixel_base + (int64_t)c.py * V.width + c.px;
+    const float ux = ((float)c.px + 0.5f - V.cx) / V.fx;
+    const float uy = ((float)c.py + 0.5f - V.cy) / V.fy;
+    c.r2 = fmaf(ux, ux, fmaf(uy, uy, 1.0f));
+    c.rlen = sqrtf(c.r2);
+    const int2 rg = ranges[tile];
+    c.start = rg.x;
+    c.end = rg.y;
+    c.rec_base = (int64_t)c.v * P;
+    return c;
+}
+
+__device__ __forceinline__ float load_m0(const Params& p, const void* moments, int64_t pix) {
+    return reinterpret_cast<const float*>(moments)[pix];   // m0 is the first plane in every storage format
+}
+
+// ---------------------------------------------------------------- pass 1
+template <int NI>
+__global__ void __launch_bounds__(TPB, 2)
+    k_adjoint_moments(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
+                      const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
+                      const float* __restrict__ recon, const void* __restrict__ moments,
+                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
+                      const float* __restrict__ dL_dP, float* __restrict__ psi_out) {
+    extern __shared__ float4 s_raw[];
+    float* s_rec = reinterpret_cast<float*>(s_raw);
+    BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
+    if (sw->n_valid == 0) c.end = c.start;
+    Recon R;
+    float C[15];
+    PixelAdj pa;
+    float psi[NPOLY];
+#pragma unroll
+    for (int k = 0; k < NPOLY; ++k) psi[k] = 0.0f;
+    float lam0 = 0.0f;
+    if (c.inside) {
+        R = load_recon(recon, npix, c.pix);
+        pi_monomials(R, C);
+        const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
+        const float O = saved[3 * npix + c.pix];
+        const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
+        pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
+    }
+    const int n = c.end - c.start;
+    const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
+    for (int b = 0; b * TPB < n; ++b) {
+        const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
+        if (c.inside) {
+            for (int k = 0; k < nb; ++k) {
+                const float* r = s_rec + k * REC;
+                if (!rect_contains(r, c.px, c.py)) continue;
+                const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
+                const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
+                pair_backward<1, NI>(p, R, C, g, a, pa.gP, psi, &lam0);
+            }
+        }
+        __syncthreads();
+    }
+    if (!c.inside) return;
+    psi[0] += p.bias_alpha * lam0 + pa.gm0;
+#pragma unroll
+    for (int k = 0; k < NPOLY; ++k) psi_out[k * npix + c.pix] = psi[k];
+}
+
+// ---------------------------------------------------------------- pass 2
+constexpr int GSTRIDE = 28;   // floats per record gradient (NGRAD padded)
+
+template <int NI>
+__global__ void __launch_bounds__(TPB, 1)
+    k_grad(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
+           const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
+           const float* __restrict__ recon, const void* __restrict__ moments, const float* __restrict__ saved,
+           const float* __restrict__ dL_drgb, const float* __restrict__ dL_dP, const float* __restrict__ psi_in,
+           float* __restrict__ grec) {
+    extern __shared__ float4 s_raw[];
+    float* s_rec = reinterpret_cast<float*>(s_raw);
+    float* s_acc = s_rec + REC * TPB;                 // [TPB][NGRAD]
+    BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
+    if (sw->n_valid == 0) c.end = c.start;
+    Recon R;
+    float C[15];
+    PixelAdj pa;
+    float psi[NPOLY];
+    if (c.inside) {
+        R = load_recon(recon, npix, c.pix);
+        pi_monomials(R, C);
+        const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
+        const float O = saved[3 * npix + c.pix];
+        const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
+        pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
+#pragma unroll
+        for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
+    }
+    const int lane = threadIdx.x & 31;
+    const int n = c.end - c.start;
+    const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
+    float dummy_psi[NPOLY];
+    float dummy_l0 = 0.0f;
+    for (int b = 0; b * TPB < n; ++b) {
+        const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
+        for (int q = threadIdx.x; q < nb * NGRAD; q += TPB) s_acc[q] = 0.0f;
+        __syncthreads();
+        for (int k = 0; k < nb; ++k) {
+            const float* r = s_rec + k * REC;
+            const bool active = c.inside && rect_contains(r, c.px, c.py);
+            if (!__any_sync(0xffffffffu, active)) continue;
+            float acc[NGRAD];
+#pragma unroll
+            for (int f = 0; f < NGRAD; ++f) acc[f] = 0.0f;
+            if (active) {
+                const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
+                const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
+                const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
+                PairOut po = pair_backward<2, NI>(p, R, C, g, a, pa.gP, dummy_psi, &dummy_l0);
+                moment_adjoint(p, R, g, psi, &po.g_mu, &po.g_Sig, &po.g_what);
+                geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, po.g_mu, po.g_Sig, po.g_what, acc);
+                acc[G_RGB + 0] = pa.gS[0] * po.O;
+                acc[G_RGB + 1] = pa.gS[1] * po.O;
+                acc[G_RGB + 2] = pa.gS[2] * po.O;
+            }
+#pragma unroll
+            for (int f = 0; f < NGRAD; ++f) {
+                float v = acc[f];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                acc[f] = v;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int f = 0; f < NGRAD; ++f) atomicAdd(&s_acc[k * NGRAD + f], acc[f]);
+            }
+        }
+        __syncthreads();
+        const int first = c.start + b * TPB;
+        for (int q = threadIdx.x; q < nb * NGRAD; q += TPB) {
+            const int k = q / NGRAD, f = q - k * NGRAD;
+            const float v = s_acc[q];
+            if (v != 0.0f) atomicAdd(&grec[(c.rec_base + ids[first + k]) * GSTRIDE + f], v);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- preprocessing adjoint
+MB_HD void sh_grad_basis(const Params& p, double x, double y, double z, double Y[16], double dY[16][3]) {
+    const double xx = x * x, yy = y * y, zz = z * z;
+    const float* c = p.sh_c;
+    Y[0] = c[0]; dY[0][0] = dY[0][1] = dY[0][2] = 0.0;
+    Y[1] = -c[1] * y; dY[1][0] = 0; dY[1][1] = -c[1]; dY[1][2] = 0;
+    Y[2] = c[2] * z; dY[2][0] = 0; dY[2][1] = 0; dY[2][2] = c[2];
+    Y[3] = -c[3] * x; dY[3][0] = -c[3]; dY[3][1] = 0; dY[3][2] = 0;
+    Y[4] = c[4] * x * y; dY[4][0] = c[4] * y; dY[4][1] = c[4] * x; dY[4][2] = 0;
+    Y[5] = -c[5] * y * z; dY[5][0] = 0; dY[5][1] = -c[5] * z; dY[5][2] = -c[5] * y;
+    Y[6] = c[6] * (2 * zz - xx - yy); dY[6][0] = -2 * c[6] * x; dY[6][1] = -2 * c[6] * y; dY[6][2] = 4 * c[6] * z;
+    Y[7] = -c[7] * x * z; dY[7][0] = -c[7] * z; dY[7][1] = 0; dY[7][2] = -c[7] * x;
+    Y[8] = c[8] * (xx - yy); dY[8][0] = 2 * c[8] * x; dY[8][1] = -2 * c[8] * y; dY[8][2] = 0;
+    Y[9] = -c[9] * y * (3 * xx - yy); dY[9][0] = -6 * c[9] * x * y; dY[9][1] = -c[9] * (3 * xx - 3 * yy); dY[9][2] = 0;
+    Y[10] = c[10] * x * y * z; dY[10][0] = c[10] * y * z; dY[10][1] = c[10] * x * z; dY[10][2] = c[10] * x * y;
+    Y[11] = -c[11] * y * (4 * zz - xx - yy);
+    dY[11][0] = 2 * c[11] * x * y; dY[11][1] = -c[11] * (4 * zz - xx - 3 * yy); dY[11][2] = -8 * c[11] * y * z;
+    Y[12] = c[12] * z * (2 * zz - 3 * xx - 3 * yy);
+    dY[12][0] = -6 * c[12] * x * z; dY[12][1] = -6 * c[12] * y * z; dY[12][2] = c[12] * (6 * zz - 3 * xx - 3 * yy);
+    Y[13] = -c[13] * x * (4 * zz - xx - yy);
+    dY[13][0] = -c[13] * (4 * zz - 3 * xx - yy); dY[13][1] = 2 * c[13] * x * y; dY[13][2] = -8 * c[13] * x * z;
+    Y[14] = c[14] * z * (xx - yy); dY[14][0] = 2 * c[14] * x * z; dY[14][1] = -2 * c[14] * y * z; dY[14][2] = c[14] * (xx - yy);
+    Y[15] = -c[15] * x * (xx - 3 * yy); dY[15][0] = -c[15] * (3 * xx - 3 * yy); dY[15][1] = 6 * c[15] * x * y; dY[15][2] = 0;
+}
+
+MB_HD void preprocess_bwd_one(const Params& p, const ViewTable& vt, const float* __restrict__ means,
+                              const float* __restrict__ scales, const float* __restrict__ quats,
+                              const float* __restrict__ weights, const float* __restrict__ sh, int64_t P, int sh_deg,
+                              const float* __restrict__ rec, const float* __restrict__ grec, int64_t i,
+                              float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
+                              float* __restrict__ d_weights, float* __restrict__ d_sh) {
+    const int K = (sh_deg + 1) * (sh_deg + 1);
+    double gmu[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gw = 0;
+    double gsh[48];
+    for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0;
+    double mu[3], s[3], q[4];
+    for (int k = 0; k < 3; ++k) { mu[k] = means[3 * i + k]; s[k] = scales[3 * i + k]; }
+    for (int k = 0; k < 4; ++k) q[k] = quats[4 * i + k];
+    const double w = weights[i];
+    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const double qw = q[0] / qn, qx = q[1] / qn, qy = q[2] / qn, qz = q[3] / qn;
+    const double Rq[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                             {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                             {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+    double gRq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int v = 0; v < vt.n_views; ++v) {
+        const int64_t idx = (int64_t)v * P + i;
+        const float* r = rec + idx * REC;
+        const int flags = reinterpret_cast<const int*>(r)[R_FLAGS];
+        if (!(flags & 1)) continue;
+        const float* G = grec + idx * GSTRIDE;
+        const ViewDesc& V = vt.v[v];
+        double Rv[3][3], muc[3], Rg[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Rv[a][b] = V.R[3 * a + b];
+        for (int a = 0; a < 3; ++a) {
+            muc[a] = Rv[a][0] * mu[0] + Rv[a][1] * mu[1] + Rv[a][2] * mu[2] + (double)V.t[a];
+            for (int b = 0; b < 3; ++b) Rg[a][b] = Rv[a][0] * Rq[0][b] + Rv[a][1] * Rq[1][b] + Rv[a][2] * Rq[2][b];
+        }
+        double M[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M[a][b] = Rg[b][a] / s[a];
+        const double fx = V.fx, fy = V.fy, cx = V.cx, cy = V.cy;
+        const double da[3] = {((double)r[R_AX] - cx) / fx, ((double)r[R_AY] - cy) / fy, 1.0};
+        double ga[3], mx[3], my[3], og[3];
+        for (int a = 0; a < 3; ++a) {
+            ga[a] = M[a][0] * da[0] + M[a][1] * da[1] + M[a][2];
+            mx[a] = M[a][0] / fx;
+            my[a] = M[a][1] / fy;
+            og[a] = -(M[a][0] * muc[0] + M[a][1] * muc[1] + M[a][2] * muc[2]);
+        }
+        double Gc0[3], Gcx[3], Gcy[3];
+        for (int k = 0; k < 3; ++k) { Gc0[k] = G[G_C0 + k]; Gcx[k] = G[G_CX + k]; Gcy[k] = G[G_CY + k]; }
+        const double Go0 = G[G_O], Gox = G[G_O + 1], Goy = G[G_O + 2];
+        // c = a x b: dL/da = b x G, dL/db = G x a
+        double Gog[3], Gga[3], Gmx[3], Gmy[3], t1[3], t2[3], t3[3];
+        cross3(ga, Gc0, t1); cross3(mx, Gcx, t2); cross3(my, Gcy, t3);
+        for (int k = 0; k < 3; ++k) Gog[k] = t1[k] + t2[k] + t3[k] + Go0 * ga[k] + Gox * mx[k] + Goy * my[k];
+        cross3(Gc0, og, t1);
+        for (int k = 0; k < 3; ++k) Gga[k] = t1[k] + (double)G[G_GA + k] + Go0 * og[k];
+        cross3(Gcx, og, t1);
+        for (int k = 0; k < 3; ++k) Gmx[k] = t1[k] + (double)G[G_MX + k] + Gox * og[k];
+        cross3(Gcy, og, t1);
+        for (int k = 0; k < 3; ++k) Gmy[k] = t1[k] + (double)G[G_MY + k] + Goy * og[k];
+        double GM[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                GM[a][b] = -Gog[a] * muc[b] + Gga[a] * da[b] + (b == 0 ? Gmx[a] / fx : 0.0) + (b == 1 ? Gmy[a] / fy : 0.0);
+        double Gmuc[3];
+        for (int b = 0; b < 3; ++b) Gmuc[b] = -(M[0][b] * Gog[0] + M[1][b] * Gog[1] + M[2][b] * Gog[2]);
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) gs[a] -= GM[a][b] * Rg[b][a] / (s[a] * s[a]);
+        double GRg[3][3];
+        for (int b = 0; b < 3; ++b)
+            for (int a = 0; a < 3; ++a) GRg[b][a] = GM[a][b] / s[a];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) gRq[a][b] += Rv[0][a] * GRg[0][b] + Rv[1][a] * GRg[1][b] + Rv[2][a] * GRg[2][b];
+        for (int b = 0; b < 3; ++b) gmu[b] += Rv[0][b] * Gmuc[0] + Rv[1][b] * Gmuc[1] + Rv[2][b] * Gmuc[2];
+        gw += (double)G[G_LNW] / w;
+        // SH colour at normalize(mu - eye)
+        double eye[3];
+        for (int a = 0; a < 3; ++a) eye[a] = -(Rv[0][a] * V.t[0] + Rv[1][a] * V.t[1] + Rv[2][a] * V.t[2]);
+        double dv[3] = {mu[0] - eye[0], mu[1] - eye[1], mu[2] - eye[2]};
+        const double dn = sqrt(dot3(dv, dv));
+        const double d[3] = {dv[0] / dn, dv[1] / dn, dv[2] / dn};
+        double Y[16], dY[16][3];
+        sh_grad_basis(p, d[0], d[1], d[2], Y, dY);
+        double gd[3] = {0, 0, 0};
+        for (int ch = 0; ch < 3; ++ch) {
+            double raw = 0.5;
+            for (int k = 0; k < K; ++k) raw += Y[k] * sh[(i * K + k) * 3 + ch];
+            if (!(raw > 0.0)) continue;
+            const double gc = G[G_RGB + ch];
+            for (int k = 0; k < K; ++k) {
+                gsh[k * 3 + ch] += gc * Y[k];
+                const double f = sh[(i * K + k) * 3 + ch];
+                for (int a = 0; a < 3; ++a) gd[a] += gc * f * dY[k][a];
+            }
+        }
+        const double dg = dot3(d, gd);
+        for (int a = 0; a < 3; ++a) gmu[a] += (gd[a] - d[a] * dg) / dn;
+    }
+    // R(q-hat) and the normalisation q-hat = q / |q|
+    double gqh[4];
+    gqh[0] = 2 * (-qz * gRq[0][1] + qy * gRq[0][2] + qz * gRq[1][0] - qx * gRq[1][2] - qy * gRq[2][0] + qx * gRq[2][1]);
+    gqh[1] = 2 * (qy * gRq[0][1] + qz * gRq[0][2] + qy * gRq[1][0] - 2 * qx * gRq[1][1] - qw * gRq[1][2] +
+                  qz * gRq[2][0] + qw * gRq[2][1] - 2 * qx * gRq[2][2]);
+    gqh[2] = 2 * (-2 * qy * gRq[0][0] + qx * gRq[0][1] + qw * gRq[0][2] + qx * gRq[1][0] + qz * gRq[1][2] -
+                  qw * gRq[2][0] + qz * gRq[2][1] - 2 * qy * gRq[2][2]);
+    gqh[3] = 2 * (-2 * qz * gRq[0][0] - qw * gRq[0][1] + qx * gRq[0][2] + qw * gRq[1][0] - 2 * qz * gRq[1][1] +
+                  qy * gRq[1][2] + qx * gRq[2][0] + qy * gRq[2][1]);
+    const double qh[4] = {qw, qx, qy, qz};
+    const double pr = qh[0] * gqh[0] + qh[1] * gqh[1] + qh[2] * gqh[2] + qh[3] * gqh[3];
+    for (int k = 0; k < 4; ++k) gq[k] = (gqh[k] - qh[k] * pr) / qn;
+    for (int k = 0; k < 3; ++k) {
+        d_means[3 * i + k] = (float)gmu[k];
+        d_scales[3 * i + k] = (float)gs[k];
+    }
+    for (int k = 0; k < 4; ++k) d_quats[4 * i + k] = (float)gq[k];
+    d_weights[i] = (float)gw;
+    for (int k = 0; k < 3 * K; ++k) d_sh[i * 3 * K + k] = (float)gsh[k];
+}
+
+__global__ void k_preprocess_bwd(Params p, ViewTable vt, const float* __restrict__ means,
+                                 const float* __restrict__ scales, const float* __restrict__ quats,
+                                 const float* __restrict__ weights, const float* __restrict__ sh, int64_t P,
+                                 int sh_deg, const float* __restrict__ rec, const float* __restrict__ grec,
+                                 float* __restrict__ d_means, float* __restrict__ d_scales,
+                                 float* __restrict__ d_quats, float* __restrict__ d_weights, float* __restrict__ d_sh) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P) return;
+    preprocess_bwd_one(p, vt, means, scales, quats, weights, sh, P, sh_deg, rec, grec, i, d_means, d_scales, d_quats,
+                       d_weights, d_sh);
+}
+
+int launch_backward(const Params& p, const ViewTable& vt, const Layout& L, char* ws, const mb3dgs_gaussians& g,
+                    const float* dL_drgb, const float* dL_dP, const mb3dgs_gaussian_grads& gr, cudaStream_t st) {
+    if (!gr.means || !gr.scales || !gr.quats || !gr.weights || !gr.sh) return MB3DGS_ERR_INVALID_ARG;
+    const float* rec = reinterpret_cast<const float*>(ws + L.rec);
+    const int32_t* ids = reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]);
+    const int2* ranges = reinterpret_cast<const int2*>(ws + L.ranges);
+    const StatusWordsB* sw = reinterpret_cast<const StatusWordsB*>(ws + L.status);
+    const float* recon = reinterpret_cast<const float*>(ws + L.recon);
+    const float* saved = reinterpret_cast<const float*>(ws + L.saved);
+    float* psi = reinterpret_cast<float*>(ws + L.dm);
+    float* grec = reinterpret_cast<float*>(ws + L.grec);
+    if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    if (L.n_tiles > 0) {
+        const size_t smem1 = sizeof(float) * REC * TPB;
+        const size_t smem2 = smem1 + sizeof(float) * NGRAD * TPB;
+        auto k1 = p.n_intervals == 3 ? k_adjoint_moments<3> : k_adjoint_moments<0>;
+        auto k2 = p.n_intervals == 3 ? k_grad<3> : k_grad<0>;
+        if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) != cudaSuccess)
+            return MB3DGS_ERR_CUDA;
+        count_launch();
+        k1<<<(unsigned)L.n_tiles, TPB, smem1, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, ws + L.moments,
+                                                    saved, dL_drgb, dL_dP, psi);
+        count_launch();
+        k2<<<(unsigned)L.n_tiles, TPB, smem2, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, ws + L.moments,
+                                                    saved, dL_drgb, dL_dP, psi, grec);
+    }
+    if (L.P > 0) {
+        count_launch();
+        k_preprocess_bwd<<<(unsigned)ceil_div64(L.P, 64), 64, 0, st>>>(p, vt, g.means, g.scales, g.quats, g.weights,
+                                                                      g.sh, L.P, g.sh_degree, rec, grec, gr.means,
+                                                                      gr.scales, gr.quats, gr.weights, gr.sh);
+    }
+    return MB3DGS_OK;
+}
+
 }  // namespace mb

@@ -1,0 +1,417 @@
+// Adjoint of the moment rasterizer (Sec. 3.3 "Adjoint Rendering", Eq. 22).
+//
+// Pass 1 (adjoint moments): per pixel, the derivative of the loss with respect
+// to the pixel's moment measure, represented as a polynomial Psi(t) of degree
+// 2n in standardised warped depth t = (y - c)/s, so that dL = int Psi d(dmu)
+// for any perturbation dmu of the raw (unnormalised, unbiased) measure.
+// Pass 2 (gradients): per (pixel, Gaussian) pair, the direct derivatives of
+// the quadrature, the penalty and the bound queries with respect to the 1D
+// Gaussian (mu, Sigma, w-hat), plus int Psi d(d mu_i) through the reverse
+// sweep of the moment recurrence, chained to the record coefficients.
+//
+// Derivative of a bound F = sum_i c_i w_i of the canonical representation:
+// with K(s, t) = sum_k h_k pi_k(s) pi_k(t) the kernel of the biased measure,
+// x_i the roots of K(., y), w_i = 1/K(x_i, x_i) and w_0 = 1/K(y, y):
+//   dw_0 / dmu  = w_0^2 K(., y)^2,
+//   dw_i / dmu  = w_i^2 K(., x_i) [K(., x_i) - 2 rho_i K(., y)],
+//                 rho_i = d1K(x_i, x_i) / d1K(x_i, y),
+//   dw_0 / dy   = -2 w_0^2 d1K(y, y),  dw_i / dy = 2 w_i^2 rho_i d1K(y, x_i)
+// (implicit differentiation of K(x_i, y) = 0 and of the Christoffel function),
+// where "d/dmu = Phi" means dF = int Phi d(dmu_b) for the biased normalised
+// measure mu_b.  For tau = m0 F with mu_b = (1-alpha) mu/m0 + alpha U:
+//   dtau = int [(1-alpha) Phi + alpha int Phi dU] d(dmu)   (dmu: raw measure).
+#pragma once
+#include "common.cuh"
+
+namespace mb {
+
+constexpr int NPOLY = NMOM;   // coefficients of a degree-2n polynomial
+
+// monomial coefficients (standardised t) of the monic orthogonal polynomials;
+// row k (k+1 entries) starts at k(k+1)/2
+MB_HD void pi_monomials(const Recon& R, float C[15]) {
+    C[0] = 1.0f;
+    C[1] = -R.al[0];
+    C[2] = 1.0f;
+    // pi_{k+1} = (t - al_k) pi_k - be_k pi_{k-1}
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const int o0 = (k - 1) * k / 2, o1 = k * (k + 1) / 2, o2 = (k + 1) * (k + 2) / 2;
+        const float a = R.al[k], b = R.be[k - 1];
+#pragma unroll
+        for (int jj = 0; jj <= k + 1; ++jj) {
+            float v = 0.0f;
+            if (jj >= 1) v += C[o1 + jj - 1];
+            if (jj <= k) v -= a * C[o1 + jj];
+            if (jj <= k - 1) v -= b * C[o0 + jj];
+            C[o2 + jj] = v;
+        }
+    }
+}
+
+// pi_k(x) and pi_k'(x), k = 0..4
+MB_HD void pis_d(const Recon& R, float x, float P[5], float D[5]) {
+    P[0] = 1.0f; D[0] = 0.0f;
+    P[1] = x - R.al[0]; D[1] = 1.0f;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const float xa = x - R.al[k], b = R.be[k - 1];
+        P[k + 1] = fmaf(xa, P[k], -b * P[k - 1]);
+        D[k + 1] = fmaf(xa, D[k], fmaf(-b, D[k - 1], P[k]));
+    }
+}
+
+// monomial coefficients of K(t, x) = sum_k h_k pi_k(x) pi_k(t)
+MB_HD void kernel_monomials(const Recon& R, const float C[15], const float P[5], float kc[5]) {
+    float e[5];
+    e[0] = 1.0f;
+#pragma unroll
+    for (int k = 1; k < 5; ++k) e[k] = R.h[k - 1] * P[k];
+#pragma unroll
+    for (int jj = 0; jj < 5; ++jj) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = jj; k < 5; ++k) s = fmaf(e[k], C[k * (k + 1) / 2 + jj], s);
+        kc[jj] = s;
+    }
+}
+
+// out += scale * a(t) * b(t)
+MB_HD void poly_mul_acc(const float a[5], const float b[5], float scale, float out[NPOLY]) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float ai = a[i] * scale;
+#pragma unroll
+        for (int jj = 0; jj < 5; ++jj) out[i + jj] = fmaf(ai, b[jj], out[i + jj]);
+    }
+}
+
+MB_HD float kdot(const Recon& R, const float Pa[5], const float Pb[5]) {
+    return Pa[0] * Pb[0] + R.h[0] * Pa[1] * Pb[1] + R.h[1] * Pa[2] * Pb[2] + R.h[2] * Pa[3] * Pb[3] +
+           R.h[3] * Pa[4] * Pb[4];
+}
+
+// Adjoint of one bound query.  Adds gq * m0 * dF/dy (standardised y) to *gy and,
+// if POLY, gq * (1 - alpha) Phi_F to psi and gq * int Phi_F dU to *lam0.
+template <bool POLY>
+MB_HD void query_adjoint(const Params& p, const Recon& R, const float C[15], const QueryRec& q, float gq, float* gy,
+                         float psi[NPOLY], float* lam0) {
+    if (R.m0 <= 0.0f || gq == 0.0f) return;
+    float Py[5], Dy[5];
+    pis_d(R, q.y, Py, Dy);
+    const float Kyy = kdot(R, Py, Py);
+    const float w0 = 1.0f / Kyy;
+    const float K1yy = kdot(R, Dy, Py);
+    const float dw0 = -2.0f * w0 * w0 * K1yy;
+    const bool left = q.j <= 2;
+    const float sgn = left ? 1.0f : -1.0f;      // sign of the root weights in F
+    const float c0 = left ? p.beta : -(1.0f - p.beta);
+    float dF = c0 * dw0;
+    float kcy[5];
+    float Ky_m[5];
+    if (POLY) {
+        kernel_monomials(R, C, Py, kcy);
+        poly_mul_acc(kcy, kcy, gq * (1.0f - p.bias_alpha) * c0 * w0 * w0, psi);
+        if (!left) psi[0] += gq * (1.0f - p.bias_alpha);      // the constant 1 of F = 1 - ...
+        float l0 = 0.0f;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            float Pm[5];
+            pis(R, (p.gl_y[m] - R.c) * R.inv_s, Pm);
+            Ky_m[m] = kdot(R, Py, Pm);
+            l0 = fmaf(p.gl_w[m], Ky_m[m] * Ky_m[m], l0);
+        }
+        *lam0 += gq * (c0 * w0 * w0 * l0 + (left ? 0.0f : 1.0f));
+    }
+    for (int r = 0; r < q.nroot; ++r) {
+        const float x = q.x[r];
+        float Px[5], Dx[5];
+        pis_d(R, x, Px, Dx);
+        const float w = fdiv_(1.0f, kdot(R, Px, Px));
+        if (!isfinite(w) || w == 0.0f) continue;
+        const float K1xx = kdot(R, Dx, Px);
+        const float K1xy = kdot(R, Dx, Py);
+        const float K1yx = kdot(R, Dy, Px);
+        const float rho = K1xy != 0.0f ? K1xx / K1xy : 0.0f;
+        dF = fmaf(sgn, 2.0f * w * w * rho * K1yx, dF);
+        if (POLY) {
+            float kcx[5];
+            kernel_monomials(R, C, Px, kcx);
+            const float s = gq * (1.0f - p.bias_alpha) * sgn * w * w;
+            poly_mul_acc(kcx, kcx, s, psi);
+            poly_mul_acc(kcx, kcy, -2.0f * rho * s, psi);
+            float l0 = 0.0f;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                float Pm[5];
+                pis(R, (p.gl_y[m] - R.c) * R.inv_s, Pm);
+                const float Kx = kdot(R, Px, Pm);
+                l0 = fmaf(p.gl_w[m], Kx * (Kx - 2.0f * rho * Ky_m[m]), l0);
+            }
+            *lam0 += gq * sgn * w * w * l0;
+        }
+    }
+    *gy = fmaf(gq * R.m0, dF, *gy);
+}
+
+struct PairOut {
+    float O;                  // O_i
+    float g_mu, g_Sig, g_what; // dL/d(mu, Sigma, w-hat) of this pair (direct part)
+};
+
+// Recomputes the pair's quadrature (Eq. 7, App. B, App. D) and back-propagates
+// L_i = a O_i + gP P_i.  MODE 1 accumulates the moment adjoint polynomial;
+// MODE 2 returns the direct derivatives with respect to (mu, Sigma, w-hat).
+template <int MODE, int NI>
+MB_HD PairOut pair_backward(const Params& p, const Recon& R, const float C[15], const Gauss1D& g, float a, float gP,
+                            float psi[NPOLY], float* lam0) {
+    constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
+    const int N = NI > 0 ? NI : p.n_intervals;
+    float t[NN], tau[NN], gt[NN], gtau[NN], dg[NN];
+    bool clampd[NN];
+    QueryRec q[NN];
+    const float ks = p.kappa * g.Sig;
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+        if (NI > 0 || j <= N) {
+            const float raw = fmaf(ks, p.x_nodes[j], g.mu);
+            const float tj = fminf(fmaxf(raw, p.t_near), p.t_far);
+            clampd[j] = tj != raw;
+            t[j] = tj;
+            float gj, dgj;
+            warp_g(p, tj, gj, dgj);
+            dg[j] = dgj;
+            tau[j] = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q[j]);
+            gt[j] = 0.0f;
+            gtau[j] = 0.0f;
+        }
+    }
+    PairOut o;
+    o.O = 0.0f;
+    o.g_mu = 0.0f;
+    o.g_Sig = 0.0f;
+    o.g_what = 0.0f;
+    const float inv2s2 = 0.5f / g.Sig2;
+    const float isq = 0.70710678118654752f / g.Sig;
+    const float tscale = g.what * g.Sig * 1.25331413731550025f;
+    const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
+    float b_prev = (t[0] - g.mu) * isq;
+    float erf_prev = erff(b_prev);
+#pragma unroll
+    for (int j = 0; j < NN - 1; ++j) {
+        if (NI > 0 || j < N) {
+            const float Delta = t[j + 1] - t[j];
+            const float dtr = tau[j + 1] - tau[j];
+            const bool pos = dtr > 0.0f;
+            const float dtau = pos ? dtr : 0.0f;
+            const float Tj = expf(-tau[j]);
+            const float d0 = t[j] - g.mu;
+            const float sig = g.what * expf(-d0 * d0 * inv2s2);
+            float ph, dph;
+            if (dtau < 1e-4f) {
+                ph = fmaf(dtau, fmaf(dtau, 1.0f / 6.0f, -0.5f), 1.0f);
+                dph = fmaf(dtau, 1.0f / 3.0f, -0.5f);
+            } else {
+                const float em = expf(-dtau);
+                ph = -expm1f(-dtau) / dtau;
+                dph = (em * (1.0f + dtau) - 1.0f) / (dtau * dtau);
+            }
+            const float term = Tj * ph * sig * Delta;
+            o.O += term;
+            const float b_next = (t[j + 1] - g.mu) * isq;
+            const float erf_next = erff(b_next);
+            const float tij = tscale * (erf_next - erf_prev);
+            const float v = fmaxf(tij - dtau, 0.0f);
+            // adjoints of term = T_j ph(dtau) sig_j Delta_j and v^2
+            gtau[j] -= a * term;
+            const float gdt = a * Tj * dph * sig * Delta - 2.0f * gP * v;
+            if (pos) {
+                gtau[j + 1] += gdt;
+                gtau[j] -= gdt;
+            }
+            if (MODE == 2) {
+                const float gsig = a * Tj * ph * Delta;
+                const float gD = a * Tj * ph * sig;
+                gt[j + 1] += gD;
+                gt[j] -= gD;
+                const float sd = gsig * sig * d0 / g.Sig2;
+                gt[j] -= sd;
+                o.g_mu += sd;
+                o.g_Sig += sd * d0 / g.Sig;
+                o.g_what += gsig * expf(-d0 * d0 * inv2s2);
+                const float gtij = 2.0f * gP * v;
+                if (gtij != 0.0f) {
+                    o.g_what += gtij * tscale * (erf_next - erf_prev) / fmaxf(g.what, 1e-30f);
+                    o.g_Sig += gtij * tij / g.Sig;
+                    const float c1 = gtij * dscale * expf(-b_next * b_next);
+                    const float c0 = -gtij * dscale * expf(-b_prev * b_prev);
+                    gt[j + 1] += c1 * isq;
+                    gt[j] += c0 * isq;
+                    o.g_mu -= (c1 + c0) * isq;
+                    o.g_Sig -= (c1 * b_next + c0 * b_prev) / g.Sig;
+                }
+            }
+            b_prev = b_next;
+            erf_prev = erf_next;
+        }
+    }
+    // through the bound queries
+#pragma unroll
+    for (int j = 0; j < NN; ++j) {
+        if (NI > 0 || j <= N) {
+            float gy = 0.0f;
+            query_adjoint<MODE == 1>(p, R, C, q[j], gtau[j], &gy, psi, lam0);
+            if (MODE == 2) {
+                gt[j] = fmaf(gy, 2.0f * dg[j] * R.inv_s, gt[j]);
+                if (!clampd[j]) {
+                    o.g_mu += gt[j];
+                    o.g_Sig = fmaf(gt[j], p.kappa * p.x_nodes[j], o.g_Sig);
+                }
+            }
+        }
+    }
+    return o;
+}
+
+// int Psi d(d mu_i): reverse sweep of the moment recurrence (Eq. 10-12, App. C)
+// written for the standardised linearised warp t = A + S (t_ray - mu).
+MB_HD void moment_adjoint(const Params& p, const Recon& R, const Gauss1D& g, const float psi[NPOLY], float* g_mu,
+                          float* g_Sig, float* g_what) {
+    // linearisation point c = max(mu, t_n): a = g(c) + g'(c)(mu - c), s = g'(c);
+    // da/dmu = s in both cases, ds/dmu = g''(mu) only when c = mu
+    const float cpt = fmaxf(g.mu, p.t_near);
+    float gm, dgm, ddgm;
+    warp_g(p, cpt, gm, dgm);
+    gm = fmaf(dgm, g.mu - cpt, gm);
+    if (g.mu > p.t_near) {
+        const float z = fmaf(p.two_over_a, cpt, 1.0f);
+        ddgm = p.G3 * (dgm / p.G2) / z;   // g'' = G3 z^(lambda-2)
+    } else {
+        ddgm = 0.0f;
+    }
+    const float A = (fmaf(2.0f, gm, -1.0f) - R.c) * R.inv_s;
+    const float S = 2.0f * dgm * R.inv_s;
+    const float dS = 2.0f * ddgm * R.inv_s;
+    const float dn = p.t_near - g.mu;
+    const float bn = dn * (0.70710678118654752f / g.Sig);
+    const float en = expf(-bn * bn);
+    const float un = fmaf(S, dn, A);
+    const float w = g.what, Sg = g.Sig, S2 = g.Sig2;
+    float M[NPOLY], up[NPOLY];
+    up[0] = 1.0f;
+#pragma unroll
+    for (int k = 1; k < NPOLY; ++k) up[k] = up[k - 1] * un;
+    M[0] = w * Sg * 1.25331413731550025f * erfcf(bn);
+    M[1] = fmaf(A, M[0], S * w * S2 * en);
+#pragma unroll
+    for (int k = 2; k < NPOLY; ++k)
+        M[k] = fmaf(A, M[k - 1], fmaf(S * S * S2 * (float)(k - 1), M[k - 2], S * w * S2 * up[k - 1] * en));
+    float Mb[NPOLY];
+#pragma unroll
+    for (int k = 0; k < NPOLY; ++k) Mb[k] = psi[k];
+    float Ab = 0.0f, Sb = 0.0f, Sgb = 0.0f, wb = 0.0f, unb = 0.0f, enb = 0.0f, bnb = 0.0f, mub = 0.0f;
+#pragma unroll
+    for (int k = NPOLY - 1; k >= 2; --k) {
+        const float c = Mb[k];
+        const float km1 = (float)(k - 1);
+        Mb[k - 1] = fmaf(A, c, Mb[k - 1]);
+        Mb[k - 2] = fmaf(S * S * S2 * km1, c, Mb[k - 2]);
+        Ab = fmaf(M[k - 1], c, Ab);
+        const float bt = w * S2 * up[k - 1] * en;    // boundary term / S
+        Sb = fmaf(2.0f * S * S2 * km1 * M[k - 2] + bt, c, Sb);
+        Sgb = fmaf(2.0f * S * S * Sg * km1 * M[k - 2] + 2.0f * S * w * Sg * up[k - 1] * en, c, Sgb);
+        wb = fmaf(S * S2 * up[k - 1] * en, c, wb);
+        unb = fmaf(S * w * S2 * km1 * up[k - 2] * en, c, unb);
+        enb = fmaf(S * w * S2 * up[k - 1], c, enb);
+    }
+    {
+        const float c = Mb[1];
+        Ab = fmaf(M[0], c, Ab);
+        Mb[0] = fmaf(A, c, Mb[0]);
+        Sb = fmaf(w * S2 * en, c, Sb);
+        wb = fmaf(S * S2 * en, c, wb);
+        Sgb = fmaf(2.0f * S * w * Sg * en, c, Sgb);
+        enb = fmaf(S * w * S2, c, enb);
+    }
+    {
+        const float c = Mb[0];
+        wb = fmaf(Sg * 1.25331413731550025f * erfcf(bn), c, wb);
+        Sgb = fmaf(M[0] / Sg, c, Sgb);
+        bnb = fmaf(-w * Sg * 1.41421356237309505f * en, c, bnb);
+    }
+    bnb = fmaf(-2.0f * bn * en, enb, bnb);
+    Ab += unb;
+    Sb = fmaf(dn, unb, Sb);
+    mub = fmaf(-S, unb, mub);
+    mub = fmaf(-(0.70710678118654752f / Sg), bnb, mub);
+    Sgb = fmaf(-bn / Sg, bnb, Sgb);
+    mub = fmaf(S, Ab, mub);
+    mub = fmaf(dS, Sb, mub);
+    *g_mu += mub;
+    *g_Sig += Sgb;
+    *g_what += wb;
+}
+
+// record-coefficient gradient layout (floats)
+enum GradField { G_C0 = 0, G_CX = 3, G_CY = 6, G_GA = 9, G_MX = 12, G_MY = 15, G_O = 18, G_LNW = 21, G_RGB = 22, NGRAD = 25 };
+
+// (mu, Sigma, w-hat) of a pair -> record coefficients (inverse of pair_gaussian)
+MB_HD void geometry_adjoint(const float* __restrict__ r, float dx, float dy, float rlen, float r2, const Gauss1D& g,
+                            float g_mu, float g_Sig, float g_what, float out[NGRAD]) {
+    const float vx = fmaf(dy, r[R_CY + 0], fmaf(dx, r[R_CX + 0], r[R_C0 + 0]));
+    const float vy = fmaf(dy, r[R_CY + 1], fmaf(dx, r[R_CX + 1], r[R_C0 + 1]));
+    const float vz = fmaf(dy, r[R_CY + 2], fmaf(dx, r[R_CX + 2], r[R_C0 + 2]));
+    const float cross2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    const float gx = fmaf(dy, r[R_MY + 0], fmaf(dx, r[R_MX + 0], r[R_GA + 0]));
+    const float gy = fmaf(dy, r[R_MY + 1], fmaf(dx, r[R_MX + 1], r[R_GA + 1]));
+    const float gz = fmaf(dy, r[R_MY + 2], fmaf(dx, r[R_MX + 2], r[R_GA + 2]));
+    const float dd = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    const float inv = 1.0f / dd;
+    const float g_dd = inv * (-0.5f * g.Sig * g_Sig - g.mu * g_mu + 0.5f * g.what * cross2 * inv * g_what);
+    const float g_od = -rlen * inv * g_mu;
+    const float g_c2 = -0.5f * g.what * inv * g_what;
+    const float dg[3] = {gx, gy, gz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gd = 2.0f * dg[k] * g_dd;
+        out[G_GA + k] += gd;
+        out[G_MX + k] += gd * dx;
+        out[G_MY + k] += gd * dy;
+    }
+    out[G_O + 0] += g_od;
+    out[G_O + 1] += g_od * dx;
+    out[G_O + 2] += g_od * dy;
+    const float v[3] = {vx, vy, vz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float gv = 2.0f * v[k] * g_c2;
+        out[G_C0 + k] += gv;
+        out[G_CX + k] += gv * dx;
+        out[G_CY + k] += gv * dy;
+    }
+    out[G_LNW] += g.what * g_what;
+}
+
+// Per-pixel backward context from the forward outputs (Eq. 15 adjoint).
+struct PixelAdj {
+    float gS[3];   // dL/d(sum L_i)
+    float gO;      // dL/dO
+    float gm0;     // dL/dm0 through the rescaling
+    float gP;      // dL/dP
+};
+
+MB_HD PixelAdj pixel_adjoint(const Params& p, float m0, const float S[3], float O, const float g[3], float gP) {
+    PixelAdj a;
+    const float Tf = expf(-m0);
+    const float op = -expm1f(-m0);
+    const float den = fmaxf(p.eps, O);
+    const float r = op / den;
+    const float gs = g[0] * S[0] + g[1] * S[1] + g[2] * S[2];
+    for (int c = 0; c < 3; ++c) a.gS[c] = r * g[c];
+    a.gO = O > p.eps ? -op * gs / (O * O) : 0.0f;
+    a.gm0 = Tf * gs / den - Tf * (g[0] * p.bg[0] + g[1] * p.bg[1] + g[2] * p.bg[2]);
+    a.gP = gP;
+    return a;
+}
+
+}  // namespace mb

@@ -28,21 +28,18 @@ enum RecField {
     R_C0 = 0,    // o_g x g_a (3)
     R_CX = 3,    // o_g x m_x (3)
     R_CY = 6,    // o_g x m_y (3)
-    R_Q00 = 9,   // |g_a|^2
-    R_Q01 = 10,  // 2 g_a.m_x
-    R_Q02 = 11,  // 2 g_a.m_y
-    R_Q11 = 12,  // |m_x|^2
-    R_Q12 = 13,  // 2 m_x.m_y
-    R_Q22 = 14,  // |m_y|^2
-    R_O0 = 15,   // o_g.g_a
-    R_OX = 16,   // o_g.m_x
-    R_OY = 17,   // o_g.m_y
-    R_LNW = 18,  // ln w
-    R_RGB = 19,  // SH colour (3)
-    R_AX = 22,   // anchor pixel-centre x (half-integer)
-    R_AY = 23,
-    R_RECT = 24, // int x0, y0, x1, y1 (inclusive pixel range; x0 > x1 = empty)
-    R_FLAGS = 28 // int: bit0 visible, bit1 full-image proxy
+    R_GA = 9,    // g_a = S^-1 R^T K^-1 (anchor, 1) (3)
+    R_MX = 12,   // m_x = S^-1 R^T e_x / f_x (3)
+    R_MY = 15,   // m_y = S^-1 R^T e_y / f_y (3)
+    R_O0 = 18,   // o_g.g_a
+    R_OX = 19,   // o_g.m_x
+    R_OY = 20,   // o_g.m_y
+    R_LNW = 21,  // ln w
+    R_RGB = 22,  // SH colour (3)
+    R_AX = 25,   // anchor pixel-centre x (half-integer)
+    R_AY = 26,
+    R_RECT = 27, // int x0, y0, x1, y1 (inclusive pixel range; x0 > x1 = empty)
+    R_FLAGS = 31 // int: bit0 visible, bit1 full-image proxy
 };
 
 struct ViewDesc {
@@ -67,7 +64,8 @@ struct Params {
     float bg[3];
     float warp_lambda;
     // g-hat(t) = G0 + G1 (1 + 2t/a)^lambda, g-hat'(t) = G2 (1 + 2t/a)^(lambda-1), a = |lambda-1|
-    float G0, G1, G2, two_over_a;
+    float G0, G1, G2, G3, two_over_a;   // g-hat''(t) = G3 (1 + 2t/a)^(lambda-2)
+    float gl_y[5], gl_w[5];   // 5-point Gauss-Legendre rule for U[-1,1] (probability weights)
     int lam_is_m15;        // lambda == -1.5: powers via rsqrt
     float x_nodes[MAX_NODES];    // standard-normal sample nodes (App. B)
     float sh_c[16];        // real SH normalisation constants
@@ -167,7 +165,11 @@ MB_HD Gauss1D pair_gaussian(const float* __restrict__ r, float dx, float dy, flo
     float vy = fmaf(dy, r[R_CY + 1], fmaf(dx, r[R_CX + 1], r[R_C0 + 1]));
     float vz = fmaf(dy, r[R_CY + 2], fmaf(dx, r[R_CX + 2], r[R_C0 + 2]));
     float cross2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
-    float dd = r[R_Q00] + dx * fmaf(dx, r[R_Q11], r[R_Q01]) + dy * fmaf(dy, r[R_Q22], fmaf(dx, r[R_Q12], r[R_Q02]));
+    // d_g = g_a + dx m_x + dy m_y as a vector: |d_g|^2 >= 0 and no squared cancellation
+    const float gx = fmaf(dy, r[R_MY + 0], fmaf(dx, r[R_MX + 0], r[R_GA + 0]));
+    const float gy = fmaf(dy, r[R_MY + 1], fmaf(dx, r[R_MX + 1], r[R_GA + 1]));
+    const float gz = fmaf(dy, r[R_MY + 2], fmaf(dx, r[R_MX + 2], r[R_GA + 2]));
+    float dd = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     float od = fmaf(dy, r[R_OY], fmaf(dx, r[R_OX], r[R_O0]));
     float inv = 1.0f / dd;
     Gauss1D g;
@@ -189,11 +191,15 @@ MB_HD bool rect_contains(const float* __restrict__ r, int px, int py) {
 // warp, I_k = int_{t_n}^inf P_k(y_t) w-hat e^{-(t-mu)^2/(2 Sigma^2)} dt obeys
 // (k+1) I_{k+1} + k I_{k-1} = (2k+1) [A I_k + S Sigma^2 (P_k(y_n) G_n + S D_k)],
 // D_k = int P_k'(y_t) G dt = sum_{j = k-1, k-3, ..} (2j+1) I_j,
-// and I_0 = m-hat_0 (Eq. 10).  Same moment space as the power moments.
+// and I_0 = m-hat_0 (Eq. 10).  Same moment space as the power moments.  The
+// warp is linearised at max(mu, t_n) (it is defined on [t_n, t_f] only).
 // ----------------------------------------------------------------------------
 MB_HD void legendre_moments(const Params& p, const Gauss1D& g, float acc[NMOM]) {
+    // g-hat lives on [t_n, t_f]: linearise at c = max(mu, t_n), u = a + s (t - mu)
+    const float cpt = fmaxf(g.mu, p.t_near);
     float a, s;
-    warp_g(p, g.mu, a, s);
+    warp_g(p, cpt, a, s);
+    a = fmaf(s, g.mu - cpt, a);
     const float A = fmaf(2.0f, a, -1.0f);
     const float S = 2.0f * s;
     const float bn = (p.t_near - g.mu) * (0.70710678118654752f / g.Sig);
@@ -294,9 +300,20 @@ MB_HD float laguerre(const Recon& R, const float e[5], float x, float lo, float 
     return x;
 }
 
+// Roots of one bound query, kept by the backward pass (standardised units).
+struct QueryRec {
+    float y;        // standardised query
+    int j;          // number of Gauss nodes below y
+    int nroot;      // roots used (0..2)
+    float x[2];     // their positions
+    float F;        // (1 - beta) L + beta U
+};
+
 // tau(eta) = m0 ((1 - beta) L + beta U) = m0 (L + beta w0) at warped depth
-// y = 2 eta - 1 (Sec. 3.2, Eq. 8).
-MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
+// y = 2 eta - 1 (Sec. 3.2, Eq. 8).  REC keeps the roots for the adjoint.
+template <bool REC>
+MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) {
+    if (REC) { rec->nroot = 0; rec->j = 0; rec->F = 0.0f; rec->y = 0.0f; }
     if (R.m0 <= 0.0f) return 0.0f;
     const float y = (y_raw - R.c) * R.inv_s;
     float P[5];
@@ -310,6 +327,7 @@ MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
     const float K = 1.0f + e[1] * P[1] + e[2] * P[2] + e[3] * P[3] + e[4] * P[4];
     const float w0 = fdiv_(1.0f, K);
     const int j = (R.z[0] < y) + (R.z[1] < y) + (R.z[2] < y) + (R.z[3] < y);
+    if (REC) { rec->y = y; rec->j = j; }
     // scale the kernel coefficients (roots are scale invariant) to keep f^2 finite
     const float sc = fdiv_(1.0f, fabsf(e[0]) + fabsf(e[1]) + fabsf(e[2]) + fabsf(e[3]) + fabsf(e[4]));
 #pragma unroll
@@ -330,21 +348,26 @@ MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
         if ((ff > 0.0f) != (fz > 0.0f)) {
             float x = left ? laguerre(R, e, far, far, zb, true) : laguerre(R, e, far, zb, far, false);
             acc += christoffel_weight(R, x);
+            if (REC) rec->x[rec->nroot++] = x;
         }
         if (j == 2) {
             // interior root in (z_1, z_2), approached from z_2 (next to eta's interval)
             float x = laguerre(R, e, R.z[1], R.z[0], R.z[1], false);
             acc += christoffel_weight(R, x);
+            if (REC) rec->x[rec->nroot++] = x;
         }
         L = left ? acc : 1.0f - w0 - acc;
     }
     L = fminf(fmaxf(L, 0.0f), 1.0f - w0);
-    return R.m0 * fmaf(beta, w0, L);
+    const float F = fmaf(beta, w0, L);
+    if (REC) rec->F = F;
+    return R.m0 * F;
 }
 
-// Modified Chebyshev algorithm (Gautschi) with monic Legendre reference
-// polynomials (a_k = 0, b_k = k^2 / (4k^2 - 1)): recurrence coefficients of
-// the biased, normalised moment measure from its Legendre moments.
+MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
+    return bound_query<false>(R, beta, y_raw, nullptr);
+}
+
 #ifndef MB_RECON_T
 #define MB_RECON_T double
 #endif

@@ -189,12 +189,11 @@ MB_HD void preprocess_one(const Params& p, const ViewDesc& V, const float* __res
         r[R_CX + k] = (float)cx[k];
         r[R_CY + k] = (float)cy[k];
     }
-    r[R_Q00] = (float)dot3(ga, ga);
-    r[R_Q01] = (float)(2.0 * dot3(ga, mx));
-    r[R_Q02] = (float)(2.0 * dot3(ga, my));
-    r[R_Q11] = (float)dot3(mx, mx);
-    r[R_Q12] = (float)(2.0 * dot3(mx, my));
-    r[R_Q22] = (float)dot3(my, my);
+    for (int k = 0; k < 3; ++k) {
+        r[R_GA + k] = (float)ga[k];
+        r[R_MX + k] = (float)mx[k];
+        r[R_MY + k] = (float)my[k];
+    }
     r[R_O0] = (float)dot3(og, ga);
     r[R_OX] = (float)dot3(og, mx);
     r[R_OY] = (float)dot3(og, my);
@@ -211,7 +210,6 @@ MB_HD void preprocess_one(const Params& p, const ViewDesc& V, const float* __res
     r[R_AY] = (float)ay;
     ri[R_RECT + 0] = x0; ri[R_RECT + 1] = y0; ri[R_RECT + 2] = x1; ri[R_RECT + 3] = y1;
     ri[R_FLAGS] = 1 | (full ? 2 : 0);
-    r[29] = 0.0f; r[30] = 0.0f; r[31] = 0.0f;
     const int tx0 = x0 / TILE, tx1 = x1 / TILE, ty0 = y0 / TILE, ty1 = y1 / TILE;
     *count = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
 }

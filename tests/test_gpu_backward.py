@@ -1,0 +1,113 @@
+"""GPU backward (mb3dgs_backward through the C ABI and the autograd Function)
+against the FP64 oracle's gradient (autograd through the oracle, itself
+pinned by central finite differences in test_oracle_grad.py).
+
+Bar: relative L2 error <= 1e-3 per parameter group (means, scales, quats,
+weights, SH), proxy rectangles held fixed on both sides."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenes
+from helpers import oracle_config
+
+pytestmark = pytest.mark.gpu
+REL = 1e-3
+torch.set_num_threads(os.cpu_count() or 8)
+NAMES = ["means", "scales", "quats", "weights", "sh"]
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11800_gb300 import RasterConfig, Rasterizer
+    return Rasterizer(RasterConfig(bg=(0.1, 0.2, 0.3)))
+
+
+def G(sc):
+    from paper_2512_11800_gb300 import GaussianTensors
+    return GaussianTensors.from_scene(sc)
+
+
+def gpu_grads(R, sc, cam, g_img, gP_img):
+    g = G(sc)
+    out = R.render(g, cam)
+    dr = torch.as_tensor(g_img.reshape(-1, 3), dtype=torch.float32, device="cuda")
+    dp = torch.as_tensor(gP_img.reshape(-1), dtype=torch.float32, device="cuda")
+    grads = R.backward(g, cam, out["capacity"], dr, dp)
+    torch.cuda.synchronize()
+    return {k: v.detach().cpu().double().numpy().reshape(-1) for k, v in grads.items()}
+
+
+def rel_errors(gg, ref):
+    return {k: float(np.linalg.norm(gg[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
+
+
+def test_backward_uniform2k_full_image(R):
+    sc, cam = scenes.workload("uniform2k_128")
+    rng = np.random.default_rng(0)
+    g_img = rng.normal(size=(cam.height, cam.width, 3))
+    gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
+    gg = gpu_grads(R, sc, cam, g_img, gP_img)
+    ref = O.render_grad(sc, cam, oracle_config(R.config), g_img, gP_img)
+    err = rel_errors(gg, ref)
+    print("uniform2k backward rel-L2", err)
+    assert max(err.values()) <= REL, err
+
+
+def test_backward_sh3_near_camera(R):
+    sc = scenes.tiny_scene(P=40, seed=9, deg=3, spread=0.5)
+    cam = scenes.look_at((0.1, 0.2, -2.0), width=48, height=40, fov_deg=55)
+    rng = np.random.default_rng(1)
+    g_img = rng.normal(size=(cam.height, cam.width, 3))
+    gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
+    gg = gpu_grads(R, sc, cam, g_img, gP_img)
+    ref = O.render_grad(sc, cam, oracle_config(R.config), g_img, gP_img)
+    err = rel_errors(gg, ref)
+    assert max(err.values()) <= REL, err
+
+
+def test_backward_full_size_crop():
+    """1M Gaussians at 1920x1080 rendered and differentiated in full; the
+    upstream gradient is non-zero on a 32x32 crop only, where the oracle
+    computes the reference gradient for all Gaussians."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11800_gb300 import Rasterizer
+    R = Rasterizer()
+    sc, cam = scenes.workload("shells1M_1080p")
+    x0, y0, s = 944, 524, 32
+    rng = np.random.default_rng(2)
+    g_img = np.zeros((cam.height, cam.width, 3))
+    gP_img = np.zeros((cam.height, cam.width))
+    g_img[y0:y0 + s, x0:x0 + s] = rng.normal(size=(s, s, 3))
+    gP_img[y0:y0 + s, x0:x0 + s] = rng.normal(size=(s, s)) * 0.1
+    gg = gpu_grads(R, sc, cam, g_img, gP_img)
+    ref = O.render_grad(sc, cam, oracle_config(), g_img[y0:y0 + s, x0:x0 + s], gP_img[y0:y0 + s, x0:x0 + s],
+                        region=(x0, y0, s, s))
+    err = rel_errors(gg, ref)
+    print("shells1M crop backward rel-L2", err, "pairs", ref["out"]["n_pairs"])
+    assert max(err.values()) <= REL, err
+
+
+def test_autograd_function_matches_direct_call(R):
+    from paper_2512_11800_gb300 import render
+    sc = scenes.scene_uniform(500, 17)
+    cam = scenes.look_at((0, 0, -3), width=40, height=40)
+    g = G(sc)
+    leaves = [getattr(g, k).clone().requires_grad_(True) for k in NAMES]
+    rgb, T, pen = render(R, cam, *leaves, sc.sh_degree)
+    target = torch.rand_like(rgb)
+    loss = ((rgb - target) ** 2).mean() + 0.1 * pen.mean()
+    auto = torch.autograd.grad(loss, leaves)
+    dr = (2.0 * (rgb - target) / rgb.numel()).detach()
+    dp = torch.full_like(pen, 0.1 / pen.numel())
+    out = R.render(g, cam)
+    direct = R.backward(g, cam, out["capacity"], dr, dp)
+    for k, a in zip(NAMES, auto):
+        b = direct[k]
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-7), k

@@ -234,3 +234,24 @@ def test_16bit_moment_storage_error_is_reported(R, dtype):
     assert torch.isfinite(out["rgb"]).all() and torch.isfinite(out["penalty"]).all()
     assert err["T"] <= TOL                 # m0 stays FP32
     assert mean_rgb < 0.02
+
+
+def test_camera_inside_the_cloud(R):
+    """Large Gaussians around and behind the camera: full-image proxies and 1D
+    means before the near bound (warp linearised at t_n).  Outputs finite and
+    within 1e-4 of the oracle on RGB and final transmittance."""
+    sc = scenes.scene_uniform(400, 31)
+    sc.means[:, 2] -= 1.5
+    sc.scales *= 3.0
+    cam = scenes.look_at((0, 0, -1.6), width=40, height=32, fov_deg=70)
+    out = R.render(G(sc), cam)
+    assert torch.isfinite(out["rgb"]).all() and torch.isfinite(out["penalty"]).all()
+    ref = O.render(sc, cam, oracle_config())
+    err = compare(out, ref, cam)
+    assert err["rgb"] <= TOL and err["T"] <= TOL, err
+
+
+def test_full_size_outputs_are_finite(R):
+    sc, cam = scenes.workload("shells1M_1080p")
+    out = R.render(G(sc), cam)
+    assert torch.isfinite(out["rgb"]).all() and torch.isfinite(out["T"]).all() and torch.isfinite(out["penalty"]).all()

@@ -127,17 +127,22 @@ CASES_1D = [(3.0, 0.05, 2.0), (2.2, 0.3, 0.7), (0.5, 0.2, 1.3), (0.05, 0.04, 3.0
             (12.0, 1.5, 0.2)]
 
 
-@pytest.mark.parametrize("mu,Sig,wh", CASES_1D)
+CASES_1D_BEHIND = [(-0.5, 0.4, 1.0), (-3.0, 2.0, 0.5), (0.005, 0.02, 2.0)]
+
+
+@pytest.mark.parametrize("mu,Sig,wh", CASES_1D + CASES_1D_BEHIND)
 def test_moments_match_quadrature(mu, Sig, wh):
     cfg = O.OracleConfig()
     m = O.gaussian_moments(T(mu), T(Sig), T(wh), cfg).numpy()
-    g, dg = (float(v) for v in O.warp(T(mu), cfg))
+    c = max(mu, cfg.t_near)                     # linearisation point (g-hat lives on [t_n, t_f])
+    gc, dg = (float(v) for v in O.warp(T(c), cfg))
+    g = gc + dg * (mu - c)
     dens = lambda t: wh * math.exp(-(t - mu) ** 2 / (2 * Sig * Sig))
     for k in range(9):
         f = lambda t: (g + dg * (t - mu)) ** k * dens(t)
-        val, err = integrate.quad(f, cfg.t_near, mu + 40 * Sig, points=[mu], epsabs=1e-15, epsrel=1e-13,
-                                  limit=400)
-        assert abs(val - m[k]) <= 1e-10 * m[0] + 1e-14, (k, val, m[k])
+        val, err = integrate.quad(f, cfg.t_near, max(mu, cfg.t_near) + 40 * Sig, points=[max(mu, cfg.t_near)],
+                                  epsabs=1e-15, epsrel=1e-13, limit=400)
+        assert abs(val - m[k]) <= 1e-10 * max(m[0], abs(m[k])) + 1e-14, (k, val, m[k])
 
 
 def test_moment0_is_exact_optical_depth():
