@@ -74,129 +74,130 @@ __device__ __forceinline__ float load_m0(const Params& p, const void* moments, i
     return reinterpret_cast<const float*>(moments)[pix];   // m0 is the first plane in every storage format
 }
 
-// ---------------------------------------------------------------- pass 1
-template <int NI>
-__global__ void __launch_bounds__(TPB, 2)
-    k_adjoint_moments(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
-                      const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
-                      const float* __restrict__ recon, const void* __restrict__ moments,
-                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
-                      const float* __restrict__ dL_dP, float* __restrict__ psi_out) {
-    extern __shared__ float4 s_raw[];
-    float* s_rec = reinterpret_cast<float*>(s_raw);
-    BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
-    if (sw->n_valid == 0) c.end = c.start;
-    Recon R;
-    float C[15];
-    PixelAdj pa;
-    float psi[NPOLY];
-#pragma unroll
-    for (int k = 0; k < NPOLY; ++k) psi[k] = 0.0f;
-    float lam0 = 0.0f;
-    if (c.inside) {
-        R = load_recon(recon, npix, c.pix);
-        pi_monomials(R, C);
-        const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
-        const float O = saved[3 * npix + c.pix];
-        const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
-        pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
-    }
-    const int n = c.end - c.start;
-    const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-    for (int b = 0; b * TPB < n; ++b) {
-        const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
-        if (c.inside) {
-            for (int k = 0; k < nb; ++k) {
-                const float* r = s_rec + k * REC;
-                if (!rect_contains(r, c.px, c.py)) continue;
-                const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
-                const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
-                pair_backward<1, NI>(p, R, C, g, a, pa.gP, psi, &lam0);
-            }
-        }
-        __syncthreads();
-    }
-    if (!c.inside) return;
-    psi[0] += p.bias_alpha * lam0 + pa.gm0;
-#pragma unroll
-    for (int k = 0; k < NPOLY; ++k) psi_out[k * npix + c.pix] = psi[k];
-}
-
-// ---------------------------------------------------------------- pass 2
 constexpr int GSTRIDE = 28;   // floats per record gradient (NGRAD padded)
 
+// Adds one staged batch's per-record sums (fields 0..nf-1) to the record gradients.
+__device__ __forceinline__ void flush_batch(const float* s_acc, int nb, int nf, const int32_t* __restrict__ ids,
+                                            int first, int64_t rec_base, float* __restrict__ grec) {
+    for (int q = threadIdx.x; q < nb * nf; q += TPB) {
+        const int k = q / nf, f = q - k * nf;
+        const float v = s_acc[k * NGRAD + f];
+        if (v != 0.0f) atomicAdd(&grec[(rec_base + ids[first + k]) * GSTRIDE + f], v);
+    }
+}
+
+// ---------------------------------------------------------------- pass 1
+// Per pair: the quadrature, penalty and bound-query adjoint.  The direct
+// derivatives go through the record geometry to the per-record gradients;
+// the bound derivatives sum into the pixel's Phi, written out as the moment
+// adjoint polynomial psi.
 template <int NI>
-__global__ void __launch_bounds__(TPB, 1)
-    k_grad(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
-           const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
-           const float* __restrict__ recon, const void* __restrict__ moments, const float* __restrict__ saved,
-           const float* __restrict__ dL_drgb, const float* __restrict__ dL_dP, const float* __restrict__ psi_in,
-           float* __restrict__ grec) {
+__global__ void __launch_bounds__(TPB, 2)
+    k_bwd_quadrature(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
+                     const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
+                     const float* __restrict__ recon, const void* __restrict__ moments,
+                     const float* __restrict__ saved, const float* __restrict__ dL_drgb,
+                     const float* __restrict__ dL_dP, float* __restrict__ psi_out, float* __restrict__ grec) {
     extern __shared__ float4 s_raw[];
     float* s_rec = reinterpret_cast<float*>(s_raw);
     float* s_acc = s_rec + REC * TPB;                 // [TPB][NGRAD]
     BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
     if (sw->n_valid == 0) c.end = c.start;
     Recon R;
-    float C[15];
     PixelAdj pa;
-    float psi[NPOLY];
+    float B[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) B[k] = 0.0f;
     if (c.inside) {
         R = load_recon(recon, npix, c.pix);
-        pi_monomials(R, C);
         const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
         const float O = saved[3 * npix + c.pix];
         const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
         pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
+    }
+    const int lane = threadIdx.x & 31;
+    const int n = c.end - c.start;
+    const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
+    for (int b = 0; b * TPB < n; ++b) {
+        for (int q = threadIdx.x; q < TPB * NGRAD; q += TPB) s_acc[q] = 0.0f;
+        const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
+        for (int k = 0; k < nb; ++k) {
+            const float* r = s_rec + k * REC;
+            const bool active = c.inside && rect_contains(r, c.px, c.py);
+            if (!__any_sync(0xffffffffu, active)) continue;
+            float acc[32];
+#pragma unroll
+            for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
+            if (active) {
+                const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
+                const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
+                const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
+                const PairOut po = pair_backward<NI>(p, R, g, a, pa.gP, B);
+                geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, po.g_mu, po.g_Sig, po.g_what, acc);
+                acc[G_RGB + 0] = pa.gS[0] * po.O;
+                acc[G_RGB + 1] = pa.gS[1] * po.O;
+                acc[G_RGB + 2] = pa.gS[2] * po.O;
+            }
+            const float v = reduce_scatter32(acc);
+            if (lane < NGRAD && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+        }
+        __syncthreads();
+        flush_batch(s_acc, nb, NGRAD, ids, c.start + b * TPB, c.rec_base, grec);
+        __syncthreads();
+    }
+    if (!c.inside) return;
+    float psi[NPOLY];
+    phi_monomials(R, B, psi);
+    finish_moment_adjoint(p, R, pa.gm0, psi);
+#pragma unroll
+    for (int k = 0; k < NPOLY; ++k) psi_out[k * npix + c.pix] = psi[k];
+}
+
+// ---------------------------------------------------------------- pass 2
+// Per pair: int psi d(d mu_i) through the reverse sweep of the moment
+// recurrence, chained to the record geometry (fields before G_RGB).
+__global__ void __launch_bounds__(TPB, 3)
+    k_bwd_moments(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
+                  const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
+                  const float* __restrict__ recon, const float* __restrict__ psi_in, float* __restrict__ grec) {
+    extern __shared__ float4 s_raw[];
+    float* s_rec = reinterpret_cast<float*>(s_raw);
+    float* s_acc = s_rec + REC * TPB;                 // [TPB][NGRAD]
+    BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
+    if (sw->n_valid == 0) c.end = c.start;
+    Recon R;                                          // only the standardisation (c, 1/s) is used
+    float psi[NPOLY];
+    if (c.inside) {
+        R.c = recon[1 * npix + c.pix];
+        R.inv_s = recon[2 * npix + c.pix];
 #pragma unroll
         for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
     }
     const int lane = threadIdx.x & 31;
     const int n = c.end - c.start;
     const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-    float dummy_psi[NPOLY];
-    float dummy_l0 = 0.0f;
     for (int b = 0; b * TPB < n; ++b) {
+        for (int q = threadIdx.x; q < TPB * NGRAD; q += TPB) s_acc[q] = 0.0f;
         const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
-        for (int q = threadIdx.x; q < nb * NGRAD; q += TPB) s_acc[q] = 0.0f;
-        __syncthreads();
         for (int k = 0; k < nb; ++k) {
             const float* r = s_rec + k * REC;
             const bool active = c.inside && rect_contains(r, c.px, c.py);
             if (!__any_sync(0xffffffffu, active)) continue;
-            float acc[NGRAD];
+            float acc[32];
 #pragma unroll
-            for (int f = 0; f < NGRAD; ++f) acc[f] = 0.0f;
+            for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
             if (active) {
                 const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
                 const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
-                const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
-                PairOut po = pair_backward<2, NI>(p, R, C, g, a, pa.gP, dummy_psi, &dummy_l0);
-                moment_adjoint(p, R, g, psi, &po.g_mu, &po.g_Sig, &po.g_what);
-                geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, po.g_mu, po.g_Sig, po.g_what, acc);
-                acc[G_RGB + 0] = pa.gS[0] * po.O;
-                acc[G_RGB + 1] = pa.gS[1] * po.O;
-                acc[G_RGB + 2] = pa.gS[2] * po.O;
+                float g_mu = 0.0f, g_Sig = 0.0f, g_what = 0.0f;
+                moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
+                geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, g_mu, g_Sig, g_what, acc);
             }
-#pragma unroll
-            for (int f = 0; f < NGRAD; ++f) {
-                float v = acc[f];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                acc[f] = v;
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int f = 0; f < NGRAD; ++f) atomicAdd(&s_acc[k * NGRAD + f], acc[f]);
-            }
+            const float v = reduce_scatter32(acc);
+            if (lane < G_RGB && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
         }
         __syncthreads();
-        const int first = c.start + b * TPB;
-        for (int q = threadIdx.x; q < nb * NGRAD; q += TPB) {
-            const int k = q / NGRAD, f = q - k * NGRAD;
-            const float v = s_acc[q];
-            if (v != 0.0f) atomicAdd(&grec[(c.rec_base + ids[first + k]) * GSTRIDE + f], v);
-        }
+        flush_batch(s_acc, nb, G_RGB, ids, c.start + b * TPB, c.rec_base, grec);
         __syncthreads();
     }
 }
@@ -369,18 +370,17 @@ int launch_backward(const Params& p, const ViewTable& vt, const Layout& L, char*
     float* grec = reinterpret_cast<float*>(ws + L.grec);
     if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (L.n_tiles > 0) {
-        const size_t smem1 = sizeof(float) * REC * TPB;
-        const size_t smem2 = smem1 + sizeof(float) * NGRAD * TPB;
-        auto k1 = p.n_intervals == 3 ? k_adjoint_moments<3> : k_adjoint_moments<0>;
-        auto k2 = p.n_intervals == 3 ? k_grad<3> : k_grad<0>;
-        if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) != cudaSuccess)
+        const size_t smem = sizeof(float) * (REC + NGRAD) * TPB;
+        auto k1 = p.n_intervals == 3 ? k_bwd_quadrature<3> : k_bwd_quadrature<0>;
+        if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(k_bwd_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return MB3DGS_ERR_CUDA;
         count_launch();
-        k1<<<(unsigned)L.n_tiles, TPB, smem1, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, ws + L.moments,
-                                                    saved, dL_drgb, dL_dP, psi);
+        k1<<<(unsigned)L.n_tiles, TPB, smem, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, ws + L.moments,
+                                                   saved, dL_drgb, dL_dP, psi, grec);
         count_launch();
-        k2<<<(unsigned)L.n_tiles, TPB, smem2, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, ws + L.moments,
-                                                    saved, dL_drgb, dL_dP, psi, grec);
+        k_bwd_moments<<<(unsigned)L.n_tiles, TPB, smem, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, psi,
+                                                              grec);
     }
     if (L.P > 0) {
         count_launch();

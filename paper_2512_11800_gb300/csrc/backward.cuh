@@ -61,28 +61,27 @@ MB_HD void pis_d(const Recon& R, float x, float P[5], float D[5]) {
     }
 }
 
-// monomial coefficients of K(t, x) = sum_k h_k pi_k(x) pi_k(t)
-MB_HD void kernel_monomials(const Recon& R, const float C[15], const float P[5], float kc[5]) {
-    float e[5];
-    e[0] = 1.0f;
+// The bound derivative Phi(t) is a sum of products K(t, x) K(t, x') of kernel
+// polynomials, K(t, x) = sum_k e_k(x) pi_k(t) with e_k(x) = h_k pi_k(x)
+// (h_0 = 1).  It is accumulated per pixel as Phi = sum_{k<=l} B_kl pi_k pi_l,
+// 15 coefficients; B_kl sits at bidx(k, l).
+constexpr int NB = 15;
+MB_HD constexpr int bidx(int k, int l) { return k * 5 - k * (k - 1) / 2 + (l - k); }
+
+MB_HD void kernel_coeffs(const Recon& R, const float P[5], float e[5]) {
+    e[0] = P[0];
 #pragma unroll
     for (int k = 1; k < 5; ++k) e[k] = R.h[k - 1] * P[k];
-#pragma unroll
-    for (int jj = 0; jj < 5; ++jj) {
-        float s = 0.0f;
-#pragma unroll
-        for (int k = jj; k < 5; ++k) s = fmaf(e[k], C[k * (k + 1) / 2 + jj], s);
-        kc[jj] = s;
-    }
 }
 
-// out += scale * a(t) * b(t)
-MB_HD void poly_mul_acc(const float a[5], const float b[5], float scale, float out[NPOLY]) {
+// B += s sym(u v^T), i.e. Phi += s K_u K_v for K_u = sum_k u_k pi_k
+MB_HD void sym_update(float B[NB], float s, const float u[5], const float v[5]) {
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        const float ai = a[i] * scale;
+    for (int k = 0; k < 5; ++k) {
+        const float su = s * u[k], sv = s * v[k];
+        B[bidx(k, k)] = fmaf(su, v[k], B[bidx(k, k)]);
 #pragma unroll
-        for (int jj = 0; jj < 5; ++jj) out[i + jj] = fmaf(ai, b[jj], out[i + jj]);
+        for (int l = k + 1; l < 5; ++l) B[bidx(k, l)] = fmaf(su, v[l], fmaf(sv, u[l], B[bidx(k, l)]));
     }
 }
 
@@ -91,11 +90,11 @@ MB_HD float kdot(const Recon& R, const float Pa[5], const float Pb[5]) {
            R.h[3] * Pa[4] * Pb[4];
 }
 
-// Adjoint of one bound query.  Adds gq * m0 * dF/dy (standardised y) to *gy and,
-// if POLY, gq * (1 - alpha) Phi_F to psi and gq * int Phi_F dU to *lam0.
-template <bool POLY>
-MB_HD void query_adjoint(const Params& p, const Recon& R, const float C[15], const QueryRec& q, float gq, float* gy,
-                         float psi[NPOLY], float* lam0) {
+// Adjoint of one bound query.  Adds gq * m0 * dF/dy (standardised y) to *gy
+// and gq * Phi_F to B.  Both (1 - alpha) Phi and int Phi dU are linear in Phi,
+// so the bias is applied once per pixel to the summed polynomial
+// (finish_moment_adjoint).
+MB_HD void query_adjoint(const Params& p, const Recon& R, const QueryRec& q, float gq, float* gy, float B[NB]) {
     if (R.m0 <= 0.0f || gq == 0.0f) return;
     float Py[5], Dy[5];
     pis_d(R, q.y, Py, Dy);
@@ -107,23 +106,13 @@ MB_HD void query_adjoint(const Params& p, const Recon& R, const float C[15], con
     const float sgn = left ? 1.0f : -1.0f;      // sign of the root weights in F
     const float c0 = left ? p.beta : -(1.0f - p.beta);
     float dF = c0 * dw0;
-    float kcy[5];
-    float Ky_m[5];
-    if (POLY) {
-        kernel_monomials(R, C, Py, kcy);
-        poly_mul_acc(kcy, kcy, gq * (1.0f - p.bias_alpha) * c0 * w0 * w0, psi);
-        if (!left) psi[0] += gq * (1.0f - p.bias_alpha);      // the constant 1 of F = 1 - ...
-        float l0 = 0.0f;
+    float ey[5];
+    kernel_coeffs(R, Py, ey);
+    sym_update(B, gq * c0 * w0 * w0, ey, ey);
+    if (!left) B[0] += gq;      // the constant 1 of F = 1 - ...
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            float Pm[5];
-            pis(R, (p.gl_y[m] - R.c) * R.inv_s, Pm);
-            Ky_m[m] = kdot(R, Py, Pm);
-            l0 = fmaf(p.gl_w[m], Ky_m[m] * Ky_m[m], l0);
-        }
-        *lam0 += gq * (c0 * w0 * w0 * l0 + (left ? 0.0f : 1.0f));
-    }
-    for (int r = 0; r < q.nroot; ++r) {
+    for (int r = 0; r < 2; ++r) {
+        if (r >= q.nroot) break;
         const float x = q.x[r];
         float Px[5], Dx[5];
         pis_d(R, x, Px, Dx);
@@ -134,24 +123,52 @@ MB_HD void query_adjoint(const Params& p, const Recon& R, const float C[15], con
         const float K1yx = kdot(R, Dy, Px);
         const float rho = K1xy != 0.0f ? K1xx / K1xy : 0.0f;
         dF = fmaf(sgn, 2.0f * w * w * rho * K1yx, dF);
-        if (POLY) {
-            float kcx[5];
-            kernel_monomials(R, C, Px, kcx);
-            const float s = gq * (1.0f - p.bias_alpha) * sgn * w * w;
-            poly_mul_acc(kcx, kcx, s, psi);
-            poly_mul_acc(kcx, kcy, -2.0f * rho * s, psi);
-            float l0 = 0.0f;
+        // Phi += s (K_x^2 - 2 rho K_x K_y) = s sym(e_x (e_x - 2 rho e_y)^T)
+        float ex[5], v[5];
+        kernel_coeffs(R, Px, ex);
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                float Pm[5];
-                pis(R, (p.gl_y[m] - R.c) * R.inv_s, Pm);
-                const float Kx = kdot(R, Px, Pm);
-                l0 = fmaf(p.gl_w[m], Kx * (Kx - 2.0f * rho * Ky_m[m]), l0);
-            }
-            *lam0 += gq * sgn * w * w * l0;
-        }
+        for (int k = 0; k < 5; ++k) v[k] = fmaf(-2.0f * rho, ey[k], ex[k]);
+        sym_update(B, gq * sgn * w * w, ex, v);
     }
     *gy = fmaf(gq * R.m0, dF, *gy);
+}
+
+// Phi = sum_{k<=l} B_kl pi_k pi_l in standardised monomials (once per pixel).
+MB_HD void phi_monomials(const Recon& R, const float B[NB], float phi[NPOLY]) {
+    float C[15];
+    pi_monomials(R, C);
+#pragma unroll
+    for (int k = 0; k < NPOLY; ++k) phi[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float q[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // q_k = sum_{l>=k} B_kl pi_l
+#pragma unroll
+        for (int l = k; l < 5; ++l)
+#pragma unroll
+            for (int jj = 0; jj <= l; ++jj) q[jj] = fmaf(B[bidx(k, l)], C[l * (l + 1) / 2 + jj], q[jj]);
+#pragma unroll
+        for (int i = 0; i <= k; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 5; ++jj) phi[i + jj] = fmaf(C[k * (k + 1) / 2 + i], q[jj], phi[i + jj]);
+    }
+}
+
+// Moment adjoint of the pixel from the summed bound derivative Phi:
+// psi = (1 - alpha) Phi + (alpha int Phi dU + dL/dm0 through the rescaling) e_0,
+// int Phi dU by the 5-point Gauss-Legendre rule (exact for degree 2n = 8).
+MB_HD void finish_moment_adjoint(const Params& p, const Recon& R, float gm0, float psi[NPOLY]) {
+    float lam0 = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const float t = (p.gl_y[m] - R.c) * R.inv_s;
+        float v = psi[NPOLY - 1];
+#pragma unroll
+        for (int k = NPOLY - 2; k >= 0; --k) v = fmaf(v, t, psi[k]);
+        lam0 = fmaf(p.gl_w[m], v, lam0);
+    }
+#pragma unroll
+    for (int k = 0; k < NPOLY; ++k) psi[k] *= 1.0f - p.bias_alpha;
+    psi[0] += p.bias_alpha * lam0 + gm0;
 }
 
 struct PairOut {
@@ -160,11 +177,10 @@ struct PairOut {
 };
 
 // Recomputes the pair's quadrature (Eq. 7, App. B, App. D) and back-propagates
-// L_i = a O_i + gP P_i.  MODE 1 accumulates the moment adjoint polynomial;
-// MODE 2 returns the direct derivatives with respect to (mu, Sigma, w-hat).
-template <int MODE, int NI>
-MB_HD PairOut pair_backward(const Params& p, const Recon& R, const float C[15], const Gauss1D& g, float a, float gP,
-                            float psi[NPOLY], float* lam0) {
+// L_i = a O_i + gP P_i: accumulates the bound derivative Phi of the pixel into
+// B and returns the direct derivatives with respect to (mu, Sigma, w-hat).
+template <int NI>
+MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, float a, float gP, float B[NB]) {
     constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
     const int N = NI > 0 ? NI : p.n_intervals;
     float t[NN], tau[NN], gt[NN], gtau[NN], dg[NN];
@@ -229,7 +245,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const float C[15], 
                 gtau[j + 1] += gdt;
                 gtau[j] -= gdt;
             }
-            if (MODE == 2) {
+            {
                 const float gsig = a * Tj * ph * Delta;
                 const float gD = a * Tj * ph * sig;
                 gt[j + 1] += gD;
@@ -260,13 +276,11 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const float C[15], 
     for (int j = 0; j < NN; ++j) {
         if (NI > 0 || j <= N) {
             float gy = 0.0f;
-            query_adjoint<MODE == 1>(p, R, C, q[j], gtau[j], &gy, psi, lam0);
-            if (MODE == 2) {
-                gt[j] = fmaf(gy, 2.0f * dg[j] * R.inv_s, gt[j]);
-                if (!clampd[j]) {
-                    o.g_mu += gt[j];
-                    o.g_Sig = fmaf(gt[j], p.kappa * p.x_nodes[j], o.g_Sig);
-                }
+            query_adjoint(p, R, q[j], gtau[j], &gy, B);
+            gt[j] = fmaf(gy, 2.0f * dg[j] * R.inv_s, gt[j]);
+            if (!clampd[j]) {
+                o.g_mu += gt[j];
+                o.g_Sig = fmaf(gt[j], p.kappa * p.x_nodes[j], o.g_Sig);
             }
         }
     }
@@ -391,6 +405,26 @@ MB_HD void geometry_adjoint(const float* __restrict__ r, float dx, float dy, flo
     }
     out[G_LNW] += g.what * g_what;
 }
+
+#ifdef __CUDACC__
+// Warp reduce-scatter of 32 per-lane values: lane f returns the warp sum of
+// v[f] (31 shuffles instead of 32 x 5 for per-field butterflies).  All 32
+// lanes must call it.
+__device__ __forceinline__ float reduce_scatter32(float v[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+#endif
 
 // Per-pixel backward context from the forward outputs (Eq. 15 adjoint).
 struct PixelAdj {

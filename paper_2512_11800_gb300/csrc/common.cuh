@@ -348,13 +348,18 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
         if ((ff > 0.0f) != (fz > 0.0f)) {
             float x = left ? laguerre(R, e, far, far, zb, true) : laguerre(R, e, far, zb, far, false);
             acc += christoffel_weight(R, x);
-            if (REC) rec->x[rec->nroot++] = x;
+            if (REC) { rec->x[0] = x; rec->nroot = 1; }
         }
         if (j == 2) {
             // interior root in (z_1, z_2), approached from z_2 (next to eta's interval)
             float x = laguerre(R, e, R.z[1], R.z[0], R.z[1], false);
             acc += christoffel_weight(R, x);
-            if (REC) rec->x[rec->nroot++] = x;
+            if (REC) {   // static indices keep the record in registers
+                const bool second = rec->nroot > 0;
+                rec->x[1] = second ? x : rec->x[1];
+                rec->x[0] = second ? rec->x[0] : x;
+                rec->nroot += 1;
+            }
         }
         L = left ? acc : 1.0f - w0 - acc;
     }
