@@ -1,12 +1,19 @@
 """Benchmark of the moment-based Gaussian rasterizer on one GB300.
 
-One step = one pass of the hot path over the 1,000,000-Gaussian scene
-(64 anisotropic clusters + interpenetrating low-density shells, SH degree 3)
-rendered at 1920x1080: preprocess -> tile binning -> moment pass ->
-per-pixel reconstruction -> quadrature pass (+ backward when enabled).
-Prints one JSON line (see the module's contract in the design doc).
+Default workload: the 1,000,000-Gaussian scene (64 anisotropic clusters +
+interpenetrating low-density shells, SH degree 3) at 1920x1080.  One step =
+the whole hot path: preprocess -> tile binning -> moment pass -> per-pixel
+reconstruction -> quadrature pass -> L2-loss gradient against a random
+target -> backward (quadrature/bound adjoint, moment adjoint, preprocessing
+adjoint).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--forward-only] [--workload shells1M_1080p|batch16]
+
+--workload batch16: the same scene seen by 16 views of uneven resolution
+(640x360 / 1280x720 / 1920x1080), the whole fwd+bwd step captured in one
+CUDA graph and replayed, next to 16 sequential single-view render+backward
+calls.
 
 With N > 1 (launched by torchrun) every rank renders its own replica of the
 workload (the path has no data exchange); rank 0 prints the aggregate.
@@ -14,6 +21,7 @@ workload (the path has no data exchange); rank 0 prints the aggregate.
 from __future__ import annotations
 
 import argparse
+import ctypes as C
 import json
 import os
 import statistics
@@ -35,22 +43,21 @@ METRIC = "Mpixel/s fwd and fwd+bwd, 1M Gaussians @1080p; fraction of roofline; e
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
+# Executed FP32 work per (pixel, Gaussian) pair (FADD + FMUL + 2 FFMA, from
+# ncu's per-opcode thread instruction counts of each kernel on the 200k/720p
+# workload divided by its pixel pairs).  The ALU roofline of a kernel is
+# this work over its time against the FP32 peak.
+FP32_FLOPS_PER_PAIR = {
+    "k_shade": 1854.0,
+    "k_bwd_quadrature": 2600.0,
+}
+
 
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
-
-
-# Algorithmic FP32 work per (pixel, Gaussian) pair of the quadrature pass,
-# counted from the per-pair arithmetic ("op model").
-def shade_flops_per_pair(n_intervals=3):
-    return SHADE_FLOPS_BASE + (n_intervals + 1) * SHADE_FLOPS_PER_QUERY
-
-
-SHADE_FLOPS_BASE = 60.0        # pair geometry, sample points, quadrature/penalty bookkeeping
-SHADE_FLOPS_PER_QUERY = 330.0  # warp, standardise, pi_k, K(eta,eta), one Laguerre root solve + weight
 
 
 class ClockSampler:
@@ -108,160 +115,181 @@ def dist_setup(n_gpus):
     return None, 0, 1
 
 
-def cpu_oracle_sample(sc, cam, seconds_target=20.0):
-    """Time the FP64 oracle on a centred crop of the same workload (bounded sample)."""
+def oracle_step(sc, cam, size, with_bwd, target):
+    """One oracle step on a centred size x size crop: forward, or forward +
+    gradient of the L2 loss against the target crop (autograd in FP64)."""
     import oracle as O
-    torch.set_num_threads(os.cpu_count() or 1)
     cfg = O.OracleConfig()
-    size = 48
-    region = ((cam.width - size) // 2, (cam.height - size) // 2, size, size)
+    x0, y0 = (cam.width - size) // 2, (cam.height - size) // 2
+    region = (x0, y0, size, size)
+    if not with_bwd:
+        return O.render(sc, cam, cfg, region=region)["n_pairs"]
+    # d/drgb of mean((rgb - target)^2) over the full frame, restricted to the crop
+    rgb = O.render(sc, cam, cfg, region=region)["rgb"].numpy()
+    tg = target.reshape(cam.height, cam.width, 3)[y0:y0 + size, x0:x0 + size]
+    g = 2.0 * (rgb - tg) / (cam.width * cam.height * 3)
+    return O.render_grad(sc, cam, cfg, g, None, region=region)["out"]["n_pairs"]
+
+
+def cpu_oracle_sample(sc, cam, with_bwd, size=32):
+    """Time the FP64 oracle on a centred crop of the same workload (bounded sample)."""
+    torch.set_num_threads(os.cpu_count() or 1)
+    target = scenes.target_image(cam.height, cam.width)
     t0 = time.perf_counter()
-    out = O.render(sc, cam, cfg, region=region)
+    n_pairs = oracle_step(sc, cam, size, with_bwd, target)
     dt = time.perf_counter() - t0
     return dict(value=size * size / dt / 1e6, unit="Mpixel/s", cores=torch.get_num_threads(), kind="oracle",
-                sample="centre %dx%d crop of the 1920x1080 frame of %s (%d pairs), %.1f s" %
-                       (size, size, WORKLOAD, out["n_pairs"], dt))
+                sample="centre %dx%d crop of the 1920x1080 frame of %s (%d pixel pairs), %s, %.1f s" %
+                       (size, size, WORKLOAD, n_pairs, "forward+backward" if with_bwd else "forward", dt))
 
 
 def run_reference(args):
     """--impl reference: the FP64 CPU oracle timed on a bounded sample per step."""
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    import oracle as O
     torch.set_num_threads(os.cpu_count() or 1)
     sc, cam = scenes.workload(WORKLOAD)
-    cfg = O.OracleConfig()
+    target = scenes.target_image(cam.height, cam.width)
     size = 16
-    region = ((cam.width - size) // 2, (cam.height - size) // 2, size, size)
+    with_bwd = not args.forward_only
     for _ in range(args.warmup):
-        O.render(sc, cam, cfg, region=region)
+        oracle_step(sc, cam, size, with_bwd, target)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.render(sc, cam, cfg, region=region)
+        oracle_step(sc, cam, size, with_bwd, target)
     dt = (time.perf_counter() - t0) / args.steps
     val = size * size / dt / 1e6
+    what = "forward+backward" if with_bwd else "forward"
     line = dict(metric=METRIC, value=val, unit="Mpixel/s", impl="reference", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=dt * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD + " (centre %dx%d crop per step)" % (size, size), gaussians=1_000_000,
-                            width=1920, height=1080),
+                config={"workload": WORKLOAD + " (centre %dx%d crop per step)" % (size, size),
+                        "gaussians": 1_000_000, "width": 1920, "height": 1080, "pass": what},
                 cpu_baseline=dict(kind="oracle", cores=torch.get_num_threads(), value=val, unit="Mpixel/s",
-                                  sample="centre %dx%d crop per step" % (size, size)),
+                                  sample="centre %dx%d crop per step, %s" % (size, size, what)),
                 e2e=dict(value=val, unit="Mpixel/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forward-only", action="store_true")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        run_reference(args)
-        return
+def roofline(kernel, ms, pairs, sm_max):
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the max SM clock
+    achieved = FP32_FLOPS_PER_PAIR[kernel] * pairs / (ms * 1e-3) / 1e12
+    return dict(kernel=kernel, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                traffic=None, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel],
+                peak_note="FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock); executed FP32 flops per pixel "
+                          "pair from ncu opcode counts" % (SM_COUNT, FP32_LANES_PER_SM, sm_max))
 
+
+class Frame:
+    """Device buffers and the C-ABI stage calls of one frame (one or more views)."""
+
+    def __init__(self, R, g, cams, target, ws=None):
+        from paper_2512_11800_gb300 import _binding as B
+        self.B, self.R, self.g, self.cams = B, R, g, cams
+        self.cap, qcap = R.pair_counts(g, cams)
+        self.qcap = R.set_query_capacity(qcap)
+        nbytes = R.workspace_bytes(cams, g.P, self.cap)
+        if ws is not None:          # a shared workspace (frames run one after the other)
+            assert ws.numel() >= nbytes
+            R._ws = ws
+        out = R.render(g, cams, capacity=self.cap, query_capacity=qcap)
+        self.arr, self.nv = R.cameras(cams)
+        self.ws = R.workspace(nbytes)
+        self.gc = g.to_c()
+        self.rgb, self.T, self.pen = out["rgb"], out["T"], out["penalty"]
+        self.target = target
+        self.dl = torch.empty_like(self.rgb)
+        self.grads = {k: torch.empty_like(getattr(g, k)) for k in ["means", "scales", "quats", "weights", "sh"]}
+        gg = B.GaussianGrads()
+        gg.means, gg.scales, gg.quats = (self.grads[k].data_ptr() for k in ["means", "scales", "quats"])
+        gg.weights, gg.sh = self.grads["weights"].data_ptr(), self.grads["sh"].data_ptr()
+        self.gg = gg
+
+    def step(self, stream, with_bwd, ev=None):
+        B, R, lib = self.B, self.R, self.R.lib
+        R.set_query_capacity(self.qcap)
+        s = C.c_void_p(stream.cuda_stream)
+        cfg = C.byref(R.cfg_c)
+        wsp, wsn, cap, P = C.c_void_p(self.ws.data_ptr()), self.ws.numel(), self.cap, self.g.P
+        rec = (lambda i: ev[i].record(stream)) if ev is not None else (lambda i: None)
+        rec(0)
+        B.check(lib.mb3dgs_preprocess(cfg, C.byref(self.gc), self.arr, self.nv, wsp, wsn, cap, s), "preprocess")
+        B.check(lib.mb3dgs_bin_tiles(cfg, self.arr, self.nv, P, cap, wsp, wsn, s), "bin")
+        rec(1)
+        B.check(lib.mb3dgs_accumulate_moments(cfg, self.arr, self.nv, P, cap, wsp, wsn, None, s), "moments")
+        rec(2)
+        B.check(lib.mb3dgs_reconstruct_transmittance(cfg, self.arr, self.nv, P, cap, wsp, wsn, None, 0, None, s),
+                "recon")
+        rec(3)
+        B.check(lib.mb3dgs_shade(cfg, self.arr, self.nv, P, cap, wsp, wsn, C.c_void_p(self.rgb.data_ptr()),
+                                 C.c_void_p(self.T.data_ptr()), C.c_void_p(self.pen.data_ptr()), s), "shade")
+        rec(4)
+        if with_bwd:
+            # L2 loss against the target image (the loss itself is the caller's)
+            torch.sub(self.rgb, self.target, out=self.dl).mul_(2.0 / self.rgb.numel())
+            B.check(lib.mb3dgs_backward_quadrature(cfg, self.arr, self.nv, P, cap, wsp, wsn,
+                                                   C.c_void_p(self.dl.data_ptr()), None, s), "backward_quadrature")
+            rec(5)
+            B.check(lib.mb3dgs_backward_moments(cfg, self.arr, self.nv, P, cap, wsp, wsn, s), "backward_moments")
+            rec(6)
+            B.check(lib.mb3dgs_backward_preprocess(cfg, C.byref(self.gc), self.arr, self.nv, wsp, wsn, cap,
+                                                   C.byref(self.gg), s), "backward_preprocess")
+        else:
+            rec(5)
+            rec(6)
+        rec(7)
+
+
+STAGES = ["preprocess+bin", "moments", "reconstruct", "shade", "bwd_quadrature", "bwd_moments", "bwd_preprocess"]
+
+
+def pair_counts(R, frame):
+    st, _ = R.status()
+    tp, pp = C.c_int64(0), C.c_int64(0)
+    frame.B.check(R.lib.mb3dgs_get_pair_counts(C.c_void_p(frame.ws.data_ptr()), frame.ws.numel(), C.byref(tp),
+                                               C.byref(pp), C.c_void_p(torch.cuda.current_stream().cuda_stream)),
+                  "pair_counts")
+    return st, int(tp.value), int(pp.value)
+
+
+def run_single(args, dist, rank, world, dev):
     from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
-    from paper_2512_11800_gb300 import _binding as B
-    import ctypes as C
-
-    dist, rank, world = dist_setup(args.gpus)
-    dev = torch.device("cuda", torch.cuda.current_device())
     sc, cam = scenes.workload(WORKLOAD)
     npix = cam.width * cam.height
     R = Rasterizer(RasterConfig(), device=dev)
     g = GaussianTensors.from_scene(sc, dev)
-    cap = R.count_pairs(g, cam)
-    out = R.render(g, cam, capacity=cap)
-    stream = torch.cuda.current_stream()
-    s = C.c_void_p(stream.cuda_stream)
-    lib = R.lib
-    arr, nv = R.cameras(cam)
-    ws = R.workspace(R.workspace_bytes(cam, g.P, cap))
-    gc = g.to_c()
-    cfg = C.byref(R.cfg_c)
-    wsp, wsn = C.c_void_p(ws.data_ptr()), ws.numel()
-    rgb, T, pen = out["rgb"], out["T"], out["penalty"]
-
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
-    dL_drgb = torch.empty_like(rgb)
-    grads = {k: torch.empty_like(getattr(g, k)) for k in ["means", "scales", "quats", "weights", "sh"]}
-    gg = B.GaussianGrads()
-    gg.means, gg.scales, gg.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
-    gg.weights, gg.sh = grads["weights"].data_ptr(), grads["sh"].data_ptr()
+    fr = Frame(R, g, cam, target)
+    stream = torch.cuda.current_stream()
     with_bwd = not args.forward_only
-
-    def step(record=None):
-        if record is not None:
-            record[0].record(stream)
-        B.check(lib.mb3dgs_preprocess(cfg, C.byref(gc), arr, nv, wsp, wsn, cap, s), "preprocess")
-        B.check(lib.mb3dgs_bin_tiles(cfg, arr, nv, g.P, cap, wsp, wsn, s), "bin")
-        if record is not None:
-            record[1].record(stream)
-        B.check(lib.mb3dgs_accumulate_moments(cfg, arr, nv, g.P, cap, wsp, wsn, None, s), "moments")
-        if record is not None:
-            record[2].record(stream)
-        B.check(lib.mb3dgs_reconstruct_transmittance(cfg, arr, nv, g.P, cap, wsp, wsn, None, 0, None, s), "recon")
-        if record is not None:
-            record[3].record(stream)
-        B.check(lib.mb3dgs_shade(cfg, arr, nv, g.P, cap, wsp, wsn, C.c_void_p(rgb.data_ptr()),
-                                 C.c_void_p(T.data_ptr()), C.c_void_p(pen.data_ptr()), s), "shade")
-        if record is not None:
-            record[4].record(stream)
-        if with_bwd:
-            # L2 loss against the random target image (the loss itself is the caller's)
-            torch.sub(rgb, target, out=dL_drgb).mul_(2.0 / rgb.numel())
-            B.check(lib.mb3dgs_backward(cfg, C.byref(gc), arr, nv, wsp, wsn, cap, C.c_void_p(dL_drgb.data_ptr()),
-                                        None, C.byref(gg), s), "backward")
-        if record is not None:
-            record[5].record(stream)
-
     for _ in range(args.warmup):
-        step()
+        fr.step(stream, with_bwd)
     torch.cuda.synchronize()
-    # per-stage times (device, CUDA events on the launching stream)
-    stage = {"preprocess+bin": [], "moments": [], "reconstruct": [], "shade": [], "backward": []}
     clocks = ClockSampler()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    l0 = lib.mb3dgs_launch_count()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    l0 = R.lib.mb3dgs_launch_count()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
     t_start.record(stream)
     for k in range(args.steps):
-        step(evs[k])
+        fr.step(stream, with_bwd, evs[k])
     t_end.record(stream)
     torch.cuda.synchronize()
-    launches = lib.mb3dgs_launch_count() - l0
+    launches = R.lib.mb3dgs_launch_count() - l0
     clk = clocks.stop()
     ms = t_start.elapsed_time(t_end) / args.steps
-    for e in evs:
-        stage["preprocess+bin"].append(e[0].elapsed_time(e[1]))
-        stage["moments"].append(e[1].elapsed_time(e[2]))
-        stage["reconstruct"].append(e[2].elapsed_time(e[3]))
-        stage["shade"].append(e[3].elapsed_time(e[4]))
-        stage["backward"].append(e[4].elapsed_time(e[5]))
-    stage_ms = {k: statistics.median(v) for k, v in stage.items()}
+    stage_ms = {name: statistics.median(e[i].elapsed_time(e[i + 1]) for e in evs) for i, name in enumerate(STAGES)}
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    st, npairs_tiles = R.status()
-    # algorithmic pairs (pixel centre inside the Gaussian's rectangle), counted exactly
-    rects = torch.empty(g.P, 4, dtype=torch.int32, device=dev)
-    B.check(lib.mb3dgs_debug_tile_lists(cfg, arr, nv, g.P, cap, wsp, wsn, None, None, C.c_void_p(rects.data_ptr()), s),
-            "debug")
-    r = rects.long()
-    pairs = int(((r[:, 2] - r[:, 0] + 1).clamp(min=0) * (r[:, 3] - r[:, 1] + 1).clamp(min=0)).sum().item())
+    st, tile_pairs, pairs = pair_counts(R, fr)
 
-    # end to end through the public API: pinned host inputs -> device, render, image back to host
+    # end to end through the public API: pinned host inputs -> device, render,
+    # backward, image back to host
     host = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).pin_memory()
             for k in ["means", "scales", "quats", "weights", "sh"]}
     dev_in = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
@@ -272,41 +300,34 @@ def main():
                          sc.sh_degree)
     outbuf = dict(rgb=torch.empty(npix, 3, device=dev), T=torch.empty(npix, device=dev),
                   penalty=torch.empty(npix, device=dev))
-
     grads2 = {k: torch.empty_like(v) for k, v in dev_in.items()}
 
     def e2e_step():
         for k in host:
             dev_in[k].copy_(host[k], non_blocking=True)
-        o = R.render(g2, cam, capacity=cap, out=outbuf, penalty=True)
+        o = R.render(g2, cam, capacity=fr.cap, out=outbuf, penalty=True, query_capacity=fr.qcap)
         if with_bwd:
             dl = (o["rgb"] - target).mul_(2.0 / o["rgb"].numel())
-            R.backward(g2, cam, cap, dl, None, grads=grads2)
+            R.backward(g2, cam, fr.cap, dl, None, grads=grads2, query_capacity=fr.qcap)
         rgb_host.copy_(o["rgb"], non_blocking=True)
 
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-
     if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
+        return None
 
-    peaks = measured_peaks()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at max SM clock
-    fwd_ms = sum(stage_ms[k] for k in ["preprocess+bin", "moments", "reconstruct", "shade"])
-    flops = pairs * shade_flops_per_pair(3)
-    achieved = flops / (stage_ms["shade"] * 1e-3) / 1e12
+    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    fwd_ms = sum(stage_ms[k] for k in STAGES[:4])
+    dominant = "k_bwd_quadrature" if with_bwd and stage_ms["bwd_quadrature"] > stage_ms["shade"] else "k_shade"
+    dom_ms = stage_ms["bwd_quadrature" if dominant == "k_bwd_quadrature" else "shade"]
     line = dict(
         metric=METRIC,
         value=world * npix / (ms * 1e-3) / 1e6,
@@ -314,26 +335,169 @@ def main():
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
         fwd_mpix_s=world * npix / (fwd_ms * 1e-3) / 1e6,
-        config=dict(workload=WORKLOAD, gaussians=g.P, width=cam.width, height=cam.height, sh_degree=3,
-                    n_moments=9, n_intervals=3, pass_="forward+backward (L2 loss vs random target)" if with_bwd
-                    else "forward", l2="inputs larger than L2 (236 MB Gaussian "
-                    "parameters + 128 MB records per step)", parallelism="replicas" if world > 1 else "1 GPU"),
+        config={"workload": WORKLOAD, "gaussians": g.P, "width": cam.width, "height": cam.height, "sh_degree": 3,
+                "n_moments": 9, "n_intervals": 3,
+                "pass": "forward+backward (L2 loss vs random target)" if with_bwd else "forward",
+                "saved_queries": fr.qcap > 0,
+                "tiling": dict(tile=[R.config.tile_w, R.config.tile_h], batch=R.config.batch,
+                               schedule=R.config.schedule),
+                "l2": "inputs larger than L2 (236 MB Gaussian parameters + 128 MB records per step)",
+                "parallelism": "replicas" if world > 1 else "1 GPU"},
         stage_ms=stage_ms,
-        pairs=pairs, tile_pairs=npairs_tiles, status=st,
-        roofline=dict(kernel="k_shade", bound="alu", achieved=achieved, peak=fp32_peak, unit="TFLOP/s",
-                      frac=achieved / fp32_peak, traffic=None,
-                      peak_note="FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock, MEASURED_PEAKS.json)"
-                                % (SM_COUNT, FP32_LANES_PER_SM, sm_max),
-                      flops_per_pair=shade_flops_per_pair(3)),
+        pairs=pairs, tile_pairs=tile_pairs, status=st,
+        roofline=roofline(dominant, dom_ms, pairs, sm_max),
+        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, sm_max),
         e2e=dict(value=world * npix / (e2e_ms * 1e-3) / 1e6, unit="Mpixel/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=int(launches),
         clocks=clk,
     )
-    line["config"]["pass"] = line["config"].pop("pass_")
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(sc, cam)
-    print(json.dumps(line))
+        line["cpu_baseline"] = cpu_oracle_sample(sc, cam, with_bwd)
+    return line
+
+
+def run_batch16(args, dist, rank, world, dev):
+    """16 views of uneven resolution: fwd+bwd in one CUDA graph vs 16 sequential
+    single-view calls (eager)."""
+    from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
+    sc, _ = scenes.workload(WORKLOAD)
+    cams = scenes.multiview_cameras(16, seed=4, radius=3.0, fov_deg=60.0)
+    npix = [c.width * c.height for c in cams]
+    g = GaussianTensors.from_scene(sc, dev)
+    R = Rasterizer(RasterConfig(), device=dev)
+    # execution shape tuned on the largest view (fwd+bwd), shared by all views
+    big = max(range(len(cams)), key=lambda i: npix[i])
+    tuned = R.autotune(g, cams[big], backward=True)
+    rng = np.random.default_rng(12)
+    target = torch.as_tensor(rng.random((sum(npix), 3), dtype=np.float32), device=dev)
+    stream = torch.cuda.current_stream()
+    with_bwd = not args.forward_only
+
+    # sequential: one Frame per view sharing one workspace, eager calls
+    offs = np.concatenate([[0], np.cumsum(npix)])
+    need = 0
+    for c in cams:
+        tp, pp = R.pair_counts(g, c)
+        R.set_query_capacity(pp)
+        need = max(need, R.workspace_bytes(c, g.P, tp))
+    R._ws = None
+    shared = R.workspace(need)
+    frames = [Frame(R, g, c, target[offs[i]:offs[i + 1]], ws=shared) for i, c in enumerate(cams)]
+
+    def seq_step():
+        for f in frames:
+            f.step(stream, with_bwd)
+
+    for _ in range(args.warmup):
+        seq_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        seq_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / args.steps
+    del frames, shared
+    R._ws = None
+    torch.cuda.empty_cache()
+
+    # batched: all views in one frame, the step captured in a CUDA graph
+    fb = Frame(R, g, cams, target)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(args.warmup):
+            fb.step(side, with_bwd)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    l0 = R.lib.mb3dgs_launch_count()
+    with torch.cuda.graph(graph):
+        fb.step(torch.cuda.current_stream(), with_bwd)
+    launches = R.lib.mb3dgs_launch_count() - l0
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler()
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st, tile_pairs, pairs = pair_counts(R, fb)
+
+    # end to end: inputs from pinned host memory into the graph's input
+    # buffers, replay, rgb back to host
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(sc, k))).pin_memory()
+            for k in ["means", "scales", "quats", "weights", "sh"]}
+    rgb_host = torch.empty(sum(npix), 3, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        for k in host:
+            getattr(g, k).copy_(host[k], non_blocking=True)
+        graph.replay()
+        rgb_host.copy_(fb.rgb, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if rank != 0:
+        return None
+    tot = sum(npix)
+    return dict(
+        metric=METRIC,
+        value=world * tot / (ms * 1e-3) / 1e6,
+        unit="Mpixel/s",
+        n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+        higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+        config={"workload": "batch16_shells1M", "gaussians": g.P, "views": [[c.width, c.height] for c in cams],
+                "pixels": tot, "pass": "forward+backward" if with_bwd else "forward",
+                "saved_queries": fb.qcap > 0,
+                "tiling": dict(tile=list(tuned[:2]), batch=tuned[2], schedule=tuned[3], tuned_ms=tuned[4]),
+                "graph": "whole step in one CUDA graph", "l2": "inputs larger than L2",
+                "parallelism": "replicas" if world > 1 else "1 GPU"},
+        sequential=dict(ms_per_step=seq_ms, mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
+                        how="16 x (render + backward) single-view eager calls"),
+        speedup_vs_sequential=seq_ms / ms,
+        pairs=pairs, tile_pairs=tile_pairs, status=st,
+        e2e=dict(value=world * tot / (e2e_ms * 1e-3) / 1e6, unit="Mpixel/s",
+                 h2d_bytes_per_step=sum(v.numel() * 4 for v in host.values()),
+                 d2h_bytes_per_step=rgb_host.numel() * 4),
+        gpu_launches=int(launches),
+        clocks=clk,
+    )
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forward-only", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    dist, rank, world = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    run = run_batch16 if args.workload == "batch16" else run_single
+    line = run(args, dist, rank, world, dev)
+    if line is not None:
+        print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 

@@ -57,6 +57,10 @@ enum {
 };
 
 enum { MB3DGS_MOMENTS_F32 = 0, MB3DGS_MOMENTS_BF16 = 1, MB3DGS_MOMENTS_F16 = 2 };
+/* How the per-tile passes map tiles of all views to CTAs.  QUEUE: one wave of
+ * persistent CTAs takes tiles from an atomic queue in decreasing order of
+ * their Gaussian-list length; GRID: one CTA per tile in view/raster order. */
+enum { MB3DGS_SCHEDULE_QUEUE = 0, MB3DGS_SCHEDULE_GRID = 1 };
 enum { MB3DGS_MAX_VIEWS = 32 };
 
 /* Method parameters.  Defaults (mb3dgs_config_default) are the paper's values
@@ -77,6 +81,21 @@ typedef struct mb3dgs_config {
     float bg[3];        /* background radiance L_bg (Eq. 2); black */
     int moment_dtype;   /* storage of the per-pixel moment buffer: MB3DGS_MOMENTS_* */
     int strict;         /* 1: non-finite Gaussian parameters set MB3DGS_ERR_NUMERIC */
+    /* Execution shape (no effect on the results: every pixel visits its
+     * Gaussians in ascending id order whatever the tiling; mb3dgs_autotune
+     * picks them).  tile_w x tile_h pixels per tile with tile_w * tile_h = 256,
+     * tile_w in {8, 16, 32, 64} (0, 0: 16 x 16); batch: Gaussian records staged
+     * in shared memory at a time, a multiple of 32 up to 256 (0: 256);
+     * schedule: MB3DGS_SCHEDULE_*. */
+    int tile_w, tile_h;
+    int batch;
+    int schedule;
+    int64_t query_capacity; /* (pixel, Gaussian) pair slots in which mb3dgs_shade keeps
+                           the N+1 bound queries of every pair (64 bytes a pair) for
+                           mb3dgs_backward; 0 (default): backward recomputes them.
+                           Size it with the pixel-pair count of
+                           mb3dgs_get_pair_counts; a frame with more pairs sets
+                           MB3DGS_ERR_CAPACITY and saves none. */
 } mb3dgs_config;
 
 /* Device pointers, caller-owned, layout as in the file comment. */
@@ -160,7 +179,9 @@ int mb3dgs_reconstruct_transmittance(const mb3dgs_config* cfg, const mb3dgs_came
 /* Stage 5 -- quadrature pass (Eq. 7, App. B) with the consistency penalty
  * (App. D) and the opacity rescaling epilogue (Eq. 15).  Writes d_rgb
  * [pixel][3], d_T_final [pixel] = exp(-m0) and, if non-NULL, d_penalty
- * [pixel] = sum_i P_i.  Keeps sum_i L_i and O in the workspace for backward. */
+ * [pixel] = sum_i P_i.  Keeps sum_i L_i and O in the workspace for backward,
+ * and, when cfg->query_capacity > 0, each pair's bound queries (optical
+ * depths and kernel-polynomial roots). */
 int mb3dgs_shade(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                  int64_t pair_capacity, void* ws, size_t ws_bytes, float* d_rgb, float* d_T_final,
                  float* d_penalty, mb3dgs_stream_t stream);
@@ -180,6 +201,26 @@ int mb3dgs_render(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3
 int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
                     int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
                     const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream);
+
+/* The three stages of mb3dgs_backward, for callers that time or interleave
+ * them (same requirements as mb3dgs_backward; call them in this order).
+ * backward_quadrature (pass 1): per (pixel, Gaussian) pair the adjoint of the
+ *   quadrature, penalty and bound queries (saved by mb3dgs_shade when
+ *   cfg->query_capacity > 0, else solved again); direct derivatives go to
+ *   per-record gradients in the workspace (zeroed first), the bound
+ *   derivatives to the per-pixel moment adjoint.
+ * backward_moments (pass 2): per pair the moment adjoint through the reverse
+ *   sweep of the moment recurrence (Eq. 10-12) into the record gradients.
+ * backward_preprocess: chain rule through stage 1 to the Gaussian parameters
+ *   (every entry of *grads is written). */
+int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                               int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
+                               const float* d_dL_dpenalty, mb3dgs_stream_t stream);
+int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                            int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream);
+int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
+                               int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity,
+                               const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream);
 
 /* Size of the fixed device workspace used by mb3dgs_render_noalloc. */
 #define MB3DGS_NOALLOC_WORKSPACE_BYTES (64u << 20)
@@ -209,6 +250,30 @@ int mb3dgs_render_noalloc(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, c
  * code) and the number of (tile, Gaussian) pairs of the last binning. */
 int mb3dgs_get_status(const void* ws, size_t ws_bytes, int* status, int64_t* n_pairs, mb3dgs_stream_t stream);
 
+/* Synchronises the stream and reads, after mb3dgs_preprocess, the number of
+ * (tile, Gaussian) pairs (the pair_capacity the frame needs; valid after
+ * mb3dgs_bin_tiles) and of (pixel, Gaussian) pairs, i.e. pixel centres inside
+ * a Gaussian's proxy rectangle (the query_capacity the frame needs).
+ * Either output may be NULL. */
+int mb3dgs_get_pair_counts(const void* ws, size_t ws_bytes, int64_t* tile_pairs, int64_t* pixel_pairs,
+                           mb3dgs_stream_t stream);
+
+/* Autotuner of the execution shape (the paper has none; its tiling is its
+ * own hardware's).  For each candidate tile shape (16x16, 32x8, 8x32), batch
+ * (64, 128, 256) and schedule (QUEUE, GRID) whose workspace fits ws_bytes it
+ * counts the frame's pairs, renders once untimed and times mb3dgs_render --
+ * and mb3dgs_backward when d_dL_drgb and grads are given -- with CUDA events
+ * on the stream (best of two), then writes the fastest shape into
+ * cfg->tile_w, tile_h, batch and schedule and its time in ms into *best_ms
+ * (may be NULL).  cfg->query_capacity is kept.  Outputs go to the caller's
+ * d_rgb [pixel][3] and d_T_final [pixel]; the other fields of cfg and the
+ * scene are those of the frames to be rendered.  The forward results of
+ * every candidate are identical.  Synchronises the stream; allocates nothing;
+ * returns MB3DGS_ERR_WORKSPACE_TOO_SMALL if no candidate fits. */
+int mb3dgs_autotune(mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
+                    void* ws, size_t ws_bytes, float* d_rgb, float* d_T_final, const float* d_dL_drgb,
+                    const mb3dgs_gaussian_grads* grads, float* best_ms, mb3dgs_stream_t stream);
+
 /* Debug/test access (device outputs, async): the sorted Gaussian ids of all
  * tile lists d_ids[capacity], per-tile [start, end) d_ranges[n_tiles][2]
  * (tiles of all views, row-major per view), and per (view, Gaussian)
@@ -222,8 +287,8 @@ int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams,
  * (host counter; used to report launches per step). */
 int64_t mb3dgs_launch_count(void);
 
-/* Number of 16x16 tiles over all views (host only). */
-int64_t mb3dgs_num_tiles(const mb3dgs_camera* cams, int n_views);
+/* Number of tiles (cfg->tile_w x cfg->tile_h pixels) over all views (host only). */
+int64_t mb3dgs_num_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views);
 
 #ifdef __cplusplus
 }

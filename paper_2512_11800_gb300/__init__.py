@@ -40,15 +40,25 @@ class RasterConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     moment_dtype: str = "f32"
     strict: int = 0
+    # keep every pair's bound queries from the forward for the backward
+    # (64 B per (pixel, Gaussian) pair at N = 3); False: backward recomputes them
+    save_queries: bool = True
+    query_budget_gb: float = 48.0  # saved queries only while they fit this (and < 2^31 pairs)
+    # execution shape (results do not depend on it; Rasterizer.autotune sets it)
+    tile_w: int = 16
+    tile_h: int = 16
+    batch: int = 256
+    schedule: str = "queue"        # "queue" | "grid"
 
     def to_c(self) -> B.Config:
         c = B.Config()
-        for f in ["n", "n_intervals", "strict"]:
+        for f in ["n", "n_intervals", "strict", "tile_w", "tile_h", "batch"]:
             setattr(c, f, int(getattr(self, f)))
         for f in ["kappa", "beta", "conf_c", "warp_lambda", "t_near", "t_far", "eps", "bias_alpha", "m_min", "r_mult"]:
             setattr(c, f, float(getattr(self, f)))
         c.bg = B.c_float3(*[float(x) for x in self.bg])
         c.moment_dtype = B.MOMENTS[self.moment_dtype]
+        c.schedule = B.SCHEDULES[self.schedule]
         return c
 
 
@@ -113,6 +123,7 @@ class Rasterizer:
         self.cfg_c = self.config.to_c()
         self.device = torch.device(device)
         self._ws = None
+        self._last_qcap = 0
 
     # ------------------------------------------------------------ plumbing
     def cameras(self, cams):
@@ -138,7 +149,7 @@ class Rasterizer:
 
     def num_tiles(self, cams):
         arr, nv = self.cameras(cams)
-        return int(self.lib.mb3dgs_num_tiles(arr, nv))
+        return int(self.lib.mb3dgs_num_tiles(C.byref(self.cfg_c), arr, nv))
 
     def status(self, stream=None):
         st = C.c_int(0)
@@ -148,24 +159,80 @@ class Rasterizer:
         return int(st.value), int(n.value)
 
     # ------------------------------------------------------------ API
-    def count_pairs(self, g: GaussianTensors, cams, stream=None):
-        """(tile, Gaussian) pairs of this frame: preprocess + binning with zero
-        capacity, then one host read of the pair total."""
+    def pair_counts(self, g: GaussianTensors, cams, stream=None):
+        """((tile, Gaussian) pairs, (pixel, Gaussian) pairs) of this frame:
+        preprocess + binning with zero capacities, then one host read."""
         arr, nv = self.cameras(cams)
+        self.cfg_c.query_capacity = 0
         ws = self.workspace(self.workspace_bytes(cams, g.P, 0))
         gc = g.to_c()
         s = _stream(stream)
         B.check(self.lib.mb3dgs_preprocess(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(), 0, s),
                 "preprocess")
         B.check(self.lib.mb3dgs_bin_tiles(C.byref(self.cfg_c), arr, nv, g.P, 0, _ptr(ws), ws.numel(), s), "bin_tiles")
-        return self.status(stream)[1]
+        tp, pp = C.c_int64(0), C.c_int64(0)
+        B.check(self.lib.mb3dgs_get_pair_counts(_ptr(ws), ws.numel(), C.byref(tp), C.byref(pp), _stream(stream)),
+                "get_pair_counts")
+        return int(tp.value), int(pp.value)
 
-    def render(self, g: GaussianTensors, cams, capacity=None, stream=None, penalty=True, out=None):
-        """Full forward (mb3dgs_render).  Returns dict(rgb (Npix,3), T (Npix,),
-        penalty (Npix,)) over the concatenated views."""
+    def count_pairs(self, g: GaussianTensors, cams, stream=None):
+        """(tile, Gaussian) pairs of this frame (the pair capacity it needs)."""
+        return self.pair_counts(g, cams, stream)[0]
+
+    def autotune(self, g: GaussianTensors, cams, backward=True, stream=None):
+        """Times the frame under each execution shape (tile shape, batch,
+        schedule) and keeps the fastest (mb3dgs_autotune); the images do not
+        depend on it.  Returns (tile_w, tile_h, batch, schedule, ms)."""
         arr, nv = self.cameras(cams)
-        if capacity is None:
-            capacity = self.count_pairs(g, cams, stream)
+        shapes = [(16, 16), (32, 8), (8, 32)]
+        need, qcap = 0, 0
+        for tw, th in shapes:
+            self.cfg_c.tile_w, self.cfg_c.tile_h = tw, th
+            tp, pp = self.pair_counts(g, cams, stream)
+            qcap = self.set_query_capacity(pp)
+            need = max(need, self.workspace_bytes(cams, g.P, tp))
+        ws = self.workspace(need)
+        npix = self.num_pixels(cams)
+        rgb = torch.empty(npix, 3, device=self.device)
+        T = torch.empty(npix, device=self.device)
+        gc = g.to_c()
+        dl, gg = None, None
+        if backward:
+            dl = torch.full((npix, 3), 1.0 / (3 * npix), device=self.device)
+            grads = {k: torch.empty_like(getattr(g, k)) for k in ["means", "scales", "quats", "weights", "sh"]}
+            gg = B.GaussianGrads()
+            gg.means, gg.scales, gg.quats = grads["means"].data_ptr(), grads["scales"].data_ptr(), grads["quats"].data_ptr()
+            gg.weights, gg.sh = grads["weights"].data_ptr(), grads["sh"].data_ptr()
+        ms = C.c_float(0.0)
+        B.check(self.lib.mb3dgs_autotune(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(), _ptr(rgb),
+                                         _ptr(T), _ptr(dl), C.byref(gg) if gg is not None else None, C.byref(ms),
+                                         _stream(stream)), "autotune")
+        c = self.cfg_c
+        self.config.tile_w, self.config.tile_h, self.config.batch = int(c.tile_w), int(c.tile_h), int(c.batch)
+        self.config.schedule = {v: k for k, v in B.SCHEDULES.items()}[int(c.schedule)]
+        return self.config.tile_w, self.config.tile_h, self.config.batch, self.config.schedule, float(ms.value)
+
+    def set_query_capacity(self, n):
+        """Query slots of the following calls (0: backward recomputes the queries):
+        n when queries are saved and n pairs fit the budget, else 0."""
+        n = int(n)
+        nbytes = n * 16 * (self.config.n_intervals + 1)
+        fits = n < 2 ** 31 and nbytes <= self.config.query_budget_gb * 2 ** 30
+        self.cfg_c.query_capacity = n if (self.config.save_queries and fits) else 0
+        return int(self.cfg_c.query_capacity)
+
+    def render(self, g: GaussianTensors, cams, capacity=None, stream=None, penalty=True, out=None,
+               query_capacity=None):
+        """Full forward (mb3dgs_render).  Returns dict(rgb (Npix,3), T (Npix,),
+        penalty (Npix,)) over the concatenated views.  Without ``capacity`` (and,
+        when queries are saved, ``query_capacity``) one counting pass with a
+        host read sizes the frame."""
+        arr, nv = self.cameras(cams)
+        if capacity is None or (query_capacity is None and self.config.save_queries):
+            tp, pp = self.pair_counts(g, cams, stream)
+            capacity = tp if capacity is None else capacity
+            query_capacity = pp if query_capacity is None else query_capacity
+        qcap = self.set_query_capacity(query_capacity or 0)
         nbytes = self.workspace_bytes(cams, g.P, capacity)
         ws = self.workspace(nbytes)
         npix = self.num_pixels(cams)
@@ -177,6 +244,8 @@ class Rasterizer:
                                        _ptr(out["rgb"]), _ptr(out["T"]), _ptr(out.get("penalty")), _stream(stream)),
                 "render")
         out["capacity"] = int(capacity)
+        out["query_capacity"] = qcap
+        self._last_qcap = qcap
         return out
 
     def render_staged(self, g: GaussianTensors, cams, capacity=None, eta=None, stream=None):
@@ -186,6 +255,7 @@ class Rasterizer:
         arr, nv = self.cameras(cams)
         if capacity is None:
             capacity = self.count_pairs(g, cams, stream)
+        self.set_query_capacity(0)
         ws = self.workspace(self.workspace_bytes(cams, g.P, capacity))
         npix = self.num_pixels(cams)
         s = _stream(stream)
@@ -220,11 +290,14 @@ class Rasterizer:
         return dict(rgb=rgb, T=T, penalty=pen, moments=mom, T_eta=Tq, ids=ids[:capacity], ranges=ranges, rects=rects,
                     capacity=int(capacity))
 
-    def backward(self, g: GaussianTensors, cams, capacity, dL_drgb, dL_dP=None, stream=None, grads=None):
-        """Adjoint of the last ``render`` (same Gaussians, cameras and capacity):
-        gradients of sum(dL_drgb * rgb) + sum(dL_dP * penalty) with respect to
-        the Gaussian parameters (mb3dgs_backward)."""
+    def backward(self, g: GaussianTensors, cams, capacity, dL_drgb, dL_dP=None, stream=None, grads=None,
+                 query_capacity=None):
+        """Adjoint of the last ``render`` (same Gaussians, cameras, capacity and
+        query capacity, by default the last render's): gradients of
+        sum(dL_drgb * rgb) + sum(dL_dP * penalty) with respect to the Gaussian
+        parameters (mb3dgs_backward)."""
         arr, nv = self.cameras(cams)
+        self.set_query_capacity(self._last_qcap if query_capacity is None else query_capacity)
         ws = self._ws
         if grads is None:
             grads = {k: torch.empty_like(getattr(g, k)) for k in ["means", "scales", "quats", "weights", "sh"]}
@@ -247,13 +320,13 @@ class _RenderFn(torch.autograd.Function):
         g = GaussianTensors(means.contiguous(), scales.contiguous(), quats.contiguous(), weights.contiguous(),
                             sh.contiguous(), sh_degree)
         out = rast.render(g, cams)
-        ctx.rast, ctx.cams, ctx.g, ctx.capacity = rast, cams, g, out["capacity"]
+        ctx.rast, ctx.cams, ctx.g, ctx.capacity, ctx.qcap = rast, cams, g, out["capacity"], out["query_capacity"]
         return out["rgb"], out["T"], out["penalty"]
 
     @staticmethod
     def backward(ctx, d_rgb, d_T, d_pen):
         # the transmittance output e^{-m0} is not differentiated (treated as a diagnostic)
-        grads = ctx.rast.backward(ctx.g, ctx.cams, ctx.capacity, d_rgb, d_pen)
+        grads = ctx.rast.backward(ctx.g, ctx.cams, ctx.capacity, d_rgb, d_pen, query_capacity=ctx.qcap)
         return None, None, None, grads["means"], grads["scales"], grads["quats"], grads["weights"], grads["sh"]
 
 

@@ -13,7 +13,9 @@ class Config(C.Structure):
     _fields_ = [("n", C.c_int), ("n_intervals", C.c_int), ("kappa", C.c_float), ("beta", C.c_float),
                 ("conf_c", C.c_float), ("warp_lambda", C.c_float), ("t_near", C.c_float), ("t_far", C.c_float),
                 ("eps", C.c_float), ("bias_alpha", C.c_float), ("m_min", C.c_float), ("r_mult", C.c_float),
-                ("bg", c_float3), ("moment_dtype", C.c_int), ("strict", C.c_int)]
+                ("bg", c_float3), ("moment_dtype", C.c_int), ("strict", C.c_int),
+                ("tile_w", C.c_int), ("tile_h", C.c_int), ("batch", C.c_int), ("schedule", C.c_int),
+                ("query_capacity", C.c_int64)]
 
 
 class Gaussians(C.Structure):
@@ -32,12 +34,14 @@ class GaussianGrads(C.Structure):
 
 
 MOMENTS = {"f32": 0, "bf16": 1, "f16": 2}
+SCHEDULES = {"queue": 0, "grid": 1}
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace too small", -4: "device wait timed out",
           -5: "non-finite Gaussian parameters", -6: "unsupported configuration", -7: "tile-pair capacity exceeded"}
 
 EXPORTS = ["mb3dgs_status_string", "mb3dgs_last_cuda_error", "mb3dgs_config_default", "mb3dgs_workspace_size", "mb3dgs_preprocess",
            "mb3dgs_bin_tiles", "mb3dgs_accumulate_moments", "mb3dgs_reconstruct_transmittance", "mb3dgs_shade",
-           "mb3dgs_render", "mb3dgs_render_noalloc", "mb3dgs_backward", "mb3dgs_get_status", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count"]
+           "mb3dgs_render", "mb3dgs_render_noalloc", "mb3dgs_backward", "mb3dgs_backward_quadrature",
+           "mb3dgs_backward_moments", "mb3dgs_backward_preprocess", "mb3dgs_get_status", "mb3dgs_get_pair_counts", "mb3dgs_autotune", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count"]
 
 _lib = None
 
@@ -59,9 +63,14 @@ def _declare(lib):
         "mb3dgs_render": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, vp, vp]),
         "mb3dgs_render_noalloc": (C.c_int, [cfg, gs, cam, C.c_int, vp, vp, vp, vp, vp]),
         "mb3dgs_backward": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, gg, vp]),
+        "mb3dgs_backward_quadrature": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp]),
+        "mb3dgs_backward_moments": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp]),
+        "mb3dgs_backward_preprocess": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, gg, vp]),
         "mb3dgs_get_status": (C.c_int, [vp, sz, P(C.c_int), P(i64), vp]),
+        "mb3dgs_get_pair_counts": (C.c_int, [vp, sz, P(i64), P(i64), vp]),
+        "mb3dgs_autotune": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, vp, vp, vp, gg, P(C.c_float), vp]),
         "mb3dgs_debug_tile_lists": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp, vp]),
-        "mb3dgs_num_tiles": (i64, [cam, C.c_int]),
+        "mb3dgs_num_tiles": (i64, [cfg, cam, C.c_int]),
         "mb3dgs_launch_count": (i64, []),
     }
     for name, (res, args) in sig.items():

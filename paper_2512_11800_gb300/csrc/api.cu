@@ -8,24 +8,20 @@
 #include "common.cuh"
 
 namespace mb {
-void launch_preprocess(const Params&, const ViewTable&, const mb3dgs_gaussians&, float*, int*, int*,
-                       unsigned long long*, cudaStream_t);
+void launch_preprocess(const Params&, const ViewTable&, const mb3dgs_gaussians&, float*, int*, StatusWords*,
+                       cudaStream_t);
 void launch_binning(const ViewTable&, const Layout&, char*, cudaStream_t);
+void launch_tile_order(const Layout&, char*, cudaStream_t);
 size_t scan_tmp_elems(int64_t);
 void launch_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t);
 void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaStream_t);
 void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t);
 void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t);
-int launch_backward(const Params&, const ViewTable&, const Layout&, char*, const mb3dgs_gaussians&, const float*,
-                    const float*, const mb3dgs_gaussian_grads&, cudaStream_t);
-
-struct StatusHost {
-    int status;
-    int pad;
-    long long n_total;
-    long long n_valid;
-    unsigned long long nonfinite;
-};
+int launch_backward_quadrature(const Params&, const ViewTable&, const Layout&, char*, const float*, const float*,
+                               cudaStream_t);
+int launch_backward_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t);
+int launch_backward_preprocess(const Params&, const ViewTable&, const Layout&, char*, const mb3dgs_gaussians&,
+                               const mb3dgs_gaussian_grads&, cudaStream_t);
 
 static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
@@ -57,11 +53,25 @@ static int check_cfg(const mb3dgs_config* c) {
         !(c->m_min >= 0) || !(c->r_mult > 0) || c->warp_lambda == 0.0f || c->warp_lambda == 1.0f)
         return MB3DGS_ERR_INVALID_ARG;
     if (c->moment_dtype < 0 || c->moment_dtype > 2) return MB3DGS_ERR_INVALID_ARG;
+    if (c->tile_w != 0 || c->tile_h != 0) {
+        const int tw = c->tile_w, th = c->tile_h;
+        if (!(tw == 8 || tw == 16 || tw == 32 || tw == 64) || tw * th != TPB) return MB3DGS_ERR_UNSUPPORTED;
+    }
+    if (c->batch < 0 || c->batch > TPB || c->batch % 32 != 0) return MB3DGS_ERR_UNSUPPORTED;
+    if (c->schedule != MB3DGS_SCHEDULE_QUEUE && c->schedule != MB3DGS_SCHEDULE_GRID) return MB3DGS_ERR_INVALID_ARG;
     return MB3DGS_OK;
 }
 
-static int make_views(const mb3dgs_camera* cams, int n_views, ViewTable& vt, int64_t& npix, int64_t& ntiles) {
+static void tile_shape(const mb3dgs_config* cfg, int& tw, int& th) {
+    tw = cfg && cfg->tile_w > 0 ? cfg->tile_w : 16;
+    th = cfg && cfg->tile_h > 0 ? cfg->tile_h : 16;
+}
+
+static int make_views(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, ViewTable& vt,
+                      int64_t& npix, int64_t& ntiles) {
     if (!cams || n_views < 1 || n_views > MB3DGS_MAX_VIEWS) return MB3DGS_ERR_INVALID_ARG;
+    int tw, th;
+    tile_shape(cfg, tw, th);
     std::memset(&vt, 0, sizeof(vt));
     vt.n_views = n_views;
     npix = 0;
@@ -77,8 +87,10 @@ static int make_views(const mb3dgs_camera* cams, int n_views, ViewTable& vt, int
         }
         d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
         d.width = c.width; d.height = c.height;
-        d.tiles_x = (c.width + TILE - 1) / TILE;
-        d.tiles_y = (c.height + TILE - 1) / TILE;
+        d.tile_w = tw;
+        d.tile_h = th;
+        d.tiles_x = (c.width + tw - 1) / tw;
+        d.tiles_y = (c.height + th - 1) / th;
         d.tile_base = (int)ntiles;
         d.pixel_base = npix;
         ntiles += (int64_t)d.tiles_x * d.tiles_y;
@@ -104,7 +116,10 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     while ((int64_t(1) << bits) < ntiles) ++bits;
     L.sort_passes = (bits + 7) / 8;
     L.final_buf = L.sort_passes % 2;
+    L.qcap = cfg ? cfg->query_capacity : 0;
+    if (L.qcap < 0 || L.qcap >= (int64_t(1) << 31)) return MB3DGS_ERR_INVALID_ARG;
     L.scan_tmp_elems = std::max(scan_tmp_elems(L.VP), scan_tmp_elems((int64_t)256 * L.nb_sort));
+    if (L.qcap > 0) L.scan_tmp_elems = std::max(L.scan_tmp_elems, scan_tmp_elems(npix));
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
     L.status = take(64);
@@ -118,6 +133,8 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.vals[1] = take(sizeof(int32_t) * (size_t)cap);
     L.hist = take(sizeof(uint32_t) * 256 * (size_t)L.nb_sort);
     L.ranges = take(sizeof(int) * 2 * (size_t)ntiles);
+    L.order = take(sizeof(int) * (size_t)ntiles);
+    L.sched = take(SCHED_BYTES);
     const int md = cfg ? cfg->moment_dtype : 0;
     L.moments = take(md == MB3DGS_MOMENTS_F32 ? sizeof(float) * NMOM * (size_t)npix
                                               : sizeof(float) * (size_t)npix + 2 * (NMOM - 1) * (size_t)npix);
@@ -125,6 +142,11 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.saved = take(sizeof(float) * 4 * (size_t)npix);
     L.dm = take(sizeof(float) * NMOM * (size_t)npix);
     L.grec = take(sizeof(float) * 28 * (size_t)L.VP);
+    if (L.qcap > 0) {
+        L.npp = take(sizeof(int) * (size_t)npix);
+        L.pq_off = take(sizeof(int) * (size_t)npix);
+        L.pq = take(sizeof(float) * 4 * (size_t)(cfg->n_intervals + 1) * (size_t)L.qcap);   // one float4 a query
+    }
     L.total = o;
     return MB3DGS_OK;
 }
@@ -132,6 +154,8 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
 static void make_params(const mb3dgs_config* c, Params& p) {
     std::memset(&p, 0, sizeof(p));
     p.n_intervals = c->n_intervals;
+    p.batch = c->batch > 0 ? c->batch : TPB;
+    p.schedule = c->schedule;
     p.kappa = c->kappa; p.beta = c->beta; p.conf_c = c->conf_c; p.t_near = c->t_near; p.t_far = c->t_far;
     p.eps = c->eps; p.bias_alpha = c->bias_alpha; p.m_min = c->m_min; p.r_mult = c->r_mult;
     for (int k = 0; k < 3; ++k) p.bg[k] = c->bg[k];
@@ -195,7 +219,7 @@ static int setup(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_view
     int rc = check_cfg(cfg);
     if (rc) return rc;
     int64_t npix, ntiles;
-    rc = make_views(cams, n_views, c.vt, npix, ntiles);
+    rc = make_views(cfg, cams, n_views, c.vt, npix, ntiles);
     if (rc) return rc;
     rc = make_layout(cfg, c.vt, npix, ntiles, P, cap, c.L);
     if (rc) return rc;
@@ -257,10 +281,11 @@ int mb3dgs_config_default(mb3dgs_config* c) {
 
 int64_t mb3dgs_launch_count(void) { return (int64_t)g_launches.load(); }
 
-int64_t mb3dgs_num_tiles(const mb3dgs_camera* cams, int n_views) {
+int64_t mb3dgs_num_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views) {
+    if (cfg && check_cfg(cfg)) return -1;
     ViewTable vt;
     int64_t npix, nt;
-    if (make_views(cams, n_views, vt, npix, nt)) return -1;
+    if (make_views(cfg, cams, n_views, vt, npix, nt)) return -1;
     return nt;
 }
 
@@ -271,7 +296,7 @@ int mb3dgs_workspace_size(const mb3dgs_config* cfg, const mb3dgs_camera* cams, i
     int rc = check_cfg(cfg);
     if (rc) return rc;
     int64_t npix, nt;
-    rc = make_views(cams, n_views, c.vt, npix, nt);
+    rc = make_views(cfg, cams, n_views, c.vt, npix, nt);
     if (rc) return rc;
     rc = make_layout(cfg, c.vt, npix, nt, P, pair_capacity, c.L);
     if (rc) return rc;
@@ -289,9 +314,9 @@ int mb3dgs_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
     if (cudaMemsetAsync(w + c.L.status, 0, 64, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
-    StatusHost* sw = reinterpret_cast<StatusHost*>(w + c.L.status);
+    StatusWords* sw = reinterpret_cast<StatusWords*>(w + c.L.status);
     launch_preprocess(c.p, c.vt, *g, reinterpret_cast<float*>(w + c.L.rec), reinterpret_cast<int*>(w + c.L.counts),
-                      &sw->status, &sw->nonfinite, st);
+                      sw, st);
     return cuda_ok();
 }
 
@@ -301,6 +326,8 @@ int mb3dgs_bin_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
     launch_binning(c.vt, c.L, static_cast<char*>(ws), reinterpret_cast<cudaStream_t>(stream));
+    if (c.p.schedule == MB3DGS_SCHEDULE_QUEUE)
+        launch_tile_order(c.L, static_cast<char*>(ws), reinterpret_cast<cudaStream_t>(stream));
     return cuda_ok();
 }
 
@@ -351,34 +378,166 @@ int mb3dgs_render(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
     launch_binning(c.vt, c.L, w, st);
+    if (c.p.schedule == MB3DGS_SCHEDULE_QUEUE) launch_tile_order(c.L, w, st);
     launch_moments(c.p, c.vt, c.L, w, st);
     launch_reconstruct(c.p, c.L, w, nullptr, 0, nullptr, st);
     launch_shade(c.p, c.vt, c.L, w, d_rgb, d_T_final, d_penalty, st);
     return cuda_ok();
 }
 
+static int check_grads(const mb3dgs_gaussians* g, const mb3dgs_gaussian_grads* gr) {
+    if (!g || !gr || g->P < 0) return MB3DGS_ERR_INVALID_ARG;
+    if (g->P > 0 && (!g->means || !g->scales || !g->quats || !g->weights || !g->sh || !gr->means || !gr->scales ||
+                     !gr->quats || !gr->weights || !gr->sh))
+        return MB3DGS_ERR_INVALID_ARG;
+    return MB3DGS_OK;
+}
+
+int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                               int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
+                               const float* d_dL_dpenalty, mb3dgs_stream_t stream) {
+    if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    rc = launch_backward_quadrature(c.p, c.vt, c.L, static_cast<char*>(ws), d_dL_drgb, d_dL_dpenalty,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return rc ? rc : cuda_ok();
+}
+
+int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
+                            int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream) {
+    Ctx c;
+    int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    rc = launch_backward_moments(c.p, c.vt, c.L, static_cast<char*>(ws), reinterpret_cast<cudaStream_t>(stream));
+    return rc ? rc : cuda_ok();
+}
+
+int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
+                               int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity,
+                               const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
+    int rc = check_grads(g, grads);
+    if (rc) return rc;
+    Ctx c;
+    rc = setup(cfg, cams, n_views, g->P, pair_capacity, ws_bytes, ws, c);
+    if (rc) return rc;
+    rc = launch_backward_preprocess(c.p, c.vt, c.L, static_cast<char*>(ws), *g, *grads,
+                                    reinterpret_cast<cudaStream_t>(stream));
+    return rc ? rc : cuda_ok();
+}
+
 int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
                     void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
                     const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
-    if (!g || !d_dL_drgb || !grads) return MB3DGS_ERR_INVALID_ARG;
+    int rc = check_grads(g, grads);
+    if (rc) return rc;
+    if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
     Ctx c;
-    int rc = setup(cfg, cams, n_views, g->P, pair_capacity, ws_bytes, ws, c);
+    rc = setup(cfg, cams, n_views, g->P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
-    rc = launch_backward(c.p, c.vt, c.L, static_cast<char*>(ws), *g, d_dL_drgb, d_dL_dpenalty, *grads,
-                         reinterpret_cast<cudaStream_t>(stream));
-    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* w = static_cast<char*>(ws);
+    if ((rc = launch_backward_quadrature(c.p, c.vt, c.L, w, d_dL_drgb, d_dL_dpenalty, st))) return rc;
+    if ((rc = launch_backward_moments(c.p, c.vt, c.L, w, st))) return rc;
+    if ((rc = launch_backward_preprocess(c.p, c.vt, c.L, w, *g, *grads, st))) return rc;
     return cuda_ok();
 }
 
 int mb3dgs_get_status(const void* ws, size_t ws_bytes, int* status, int64_t* n_pairs, mb3dgs_stream_t stream) {
     if (!ws || ws_bytes < 64) return MB3DGS_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    StatusHost h;
+    StatusWords h;
     if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (status) *status = h.status;
     if (n_pairs) *n_pairs = h.n_total;
     return MB3DGS_OK;
+}
+
+int mb3dgs_get_pair_counts(const void* ws, size_t ws_bytes, int64_t* tile_pairs, int64_t* pixel_pairs,
+                           mb3dgs_stream_t stream) {
+    if (!ws || ws_bytes < 64) return MB3DGS_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    StatusWords h;
+    if (cudaMemcpyAsync(&h, ws, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    if (tile_pairs) *tile_pairs = h.n_total;
+    if (pixel_pairs) *pixel_pairs = (int64_t)h.n_pixpairs;
+    return MB3DGS_OK;
+}
+
+int mb3dgs_autotune(mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
+                    void* ws, size_t ws_bytes, float* d_rgb, float* d_T_final, const float* d_dL_drgb,
+                    const mb3dgs_gaussian_grads* grads, float* best_ms, mb3dgs_stream_t stream) {
+    if (!cfg || !g || !d_rgb || !d_T_final || (d_dL_drgb && !grads)) return MB3DGS_ERR_INVALID_ARG;
+    int rc = check_cfg(cfg);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    static const int shapes[3][2] = {{16, 16}, {32, 8}, {8, 32}};
+    static const int batches[3] = {64, 128, 256};
+    static const int schedules[2] = {MB3DGS_SCHEDULE_QUEUE, MB3DGS_SCHEDULE_GRID};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return MB3DGS_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return MB3DGS_ERR_CUDA;
+    }
+    mb3dgs_config best = *cfg;
+    float best_t = -1.0f;
+    rc = MB3DGS_OK;
+    for (int si = 0; si < 3 && rc == MB3DGS_OK; ++si) {
+        mb3dgs_config c = *cfg;
+        c.tile_w = shapes[si][0];
+        c.tile_h = shapes[si][1];
+        c.batch = 0;
+        c.schedule = MB3DGS_SCHEDULE_GRID;
+        // this tile shape's pair count (counting pass at zero capacity)
+        mb3dgs_config cc = c;
+        cc.query_capacity = 0;
+        size_t need = 0;
+        if (mb3dgs_workspace_size(&cc, cams, n_views, g->P, 0, &need) != MB3DGS_OK || need > ws_bytes) continue;
+        if ((rc = mb3dgs_preprocess(&cc, g, cams, n_views, ws, ws_bytes, 0, stream)) != MB3DGS_OK) break;
+        if ((rc = mb3dgs_bin_tiles(&cc, cams, n_views, g->P, 0, ws, ws_bytes, stream)) != MB3DGS_OK) break;
+        int64_t cap = 0;
+        if ((rc = mb3dgs_get_pair_counts(ws, ws_bytes, &cap, nullptr, stream)) != MB3DGS_OK) break;
+        if (mb3dgs_workspace_size(&c, cams, n_views, g->P, cap, &need) != MB3DGS_OK || need > ws_bytes) continue;
+        for (int bi = 0; bi < 3 && rc == MB3DGS_OK; ++bi)
+            for (int ki = 0; ki < 2 && rc == MB3DGS_OK; ++ki) {
+                c.batch = batches[bi];
+                c.schedule = schedules[ki];
+                float t_min = -1.0f;
+                for (int it = 0; it < 3 && rc == MB3DGS_OK; ++it) {
+                    if (it > 0 && cudaEventRecord(e0, st) != cudaSuccess) rc = MB3DGS_ERR_CUDA;
+                    if (rc == MB3DGS_OK)
+                        rc = mb3dgs_render(&c, g, cams, n_views, ws, ws_bytes, cap, d_rgb, d_T_final, nullptr, stream);
+                    if (rc == MB3DGS_OK && d_dL_drgb)
+                        rc = mb3dgs_backward(&c, g, cams, n_views, ws, ws_bytes, cap, d_dL_drgb, nullptr, grads, stream);
+                    if (rc == MB3DGS_OK && it > 0) {
+                        float ms = 0.0f;
+                        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                            rc = MB3DGS_ERR_CUDA;
+                        else if (t_min < 0.0f || ms < t_min)
+                            t_min = ms;
+                    }
+                }
+                if (rc == MB3DGS_OK && t_min >= 0.0f && (best_t < 0.0f || t_min < best_t)) {
+                    best_t = t_min;
+                    best = c;
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MB3DGS_OK) return rc;
+    if (best_t < 0.0f) return MB3DGS_ERR_WORKSPACE_TOO_SMALL;
+    cfg->tile_w = best.tile_w;
+    cfg->tile_h = best.tile_h;
+    cfg->batch = best.batch;
+    cfg->schedule = best.schedule;
+    if (best_ms) *best_ms = best_t;
+    return cuda_ok();
 }
 
 int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
@@ -450,7 +609,7 @@ extern "C" int mb3dgs_render_noalloc(const mb3dgs_config* cfg, const mb3dgs_gaus
     if (rc) return rc;
     ViewTable vt;
     int64_t npix, nt;
-    rc = make_views(cams, n_views, vt, npix, nt);
+    rc = make_views(cfg, cams, n_views, vt, npix, nt);
     if (rc) return rc;
     const size_t cap_bytes = (size_t)MB3DGS_NOALLOC_WORKSPACE_BYTES;
     Layout L;

@@ -1,74 +1,15 @@
-// Backward kernels: adjoint-moment pass, gradient pass, preprocessing adjoint.
-// The rescaling derivative (Eq. 15) is folded into both passes as in the
-// paper's two-pass adjoint (Sec. 3.3, App. C "Adjoint rendering"); the proxy
-// rectangles and the culling are constants.  Per-Gaussian sums over pixels use
-// a warp reduction, one shared-memory accumulator per staged record and one
-// global atomicAdd per (tile, record, field).
+// Backward kernels: quadrature/bound adjoint pass, moment adjoint pass,
+// preprocessing adjoint.  The rescaling derivative (Eq. 15) is folded into
+// the passes as in the paper's two-pass adjoint (Sec. 3.3, App. C "Adjoint
+// rendering"); the proxy rectangles and the culling are constants.
+// Per-Gaussian sums over pixels use a warp reduce-scatter, one shared-memory
+// accumulator per staged record and one global atomicAdd per (tile, record,
+// field).  Tiles come from the schedule of tile.cuh like the forward passes.
 #include "backward.cuh"
 #include "preprocess.cuh"
+#include "tile.cuh"
 
 namespace mb {
-
-struct StatusWordsB {
-    int status;
-    int pad;
-    long long n_total;
-    long long n_valid;
-    unsigned long long nonfinite;
-};
-
-__device__ __forceinline__ void cp_async16b(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-
-__device__ __forceinline__ int stage_batch_b(float* s_rec, const float* __restrict__ rec,
-                                             const int32_t* __restrict__ ids, int64_t rec_base, int start, int end,
-                                             int b) {
-    const int first = start + b * TPB;
-    const int nb = min(TPB, end - first);
-#pragma unroll
-    for (int j = 0; j < REC / 4; ++j) {
-        const int lin = j * TPB + threadIdx.x;
-        const int rr = lin >> 3, cc = lin & 7;
-        if (rr < nb) cp_async16b(s_rec + rr * REC + cc * 4, rec + (rec_base + ids[first + rr]) * REC + cc * 4);
-    }
-    asm volatile("cp.async.wait_all;\n" ::);
-    __syncthreads();
-    return nb;
-}
-
-struct BwdPixel {
-    int v, px, py;
-    bool inside;
-    int64_t pix;
-    float rlen, r2;
-    int start, end;
-    int64_t rec_base;
-};
-
-__device__ __forceinline__ BwdPixel bwd_pixel(const ViewTable& vt, const int2* __restrict__ ranges, int64_t P,
-                                              int64_t tile) {
-    BwdPixel c;
-    c.v = find_view(vt, tile);
-    const ViewDesc& V = vt.v[c.v];
-    const int lt = (int)(tile - V.tile_base);
-    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    c.px = tx * TILE + (warp & 1) * 8 + (lane & 7);
-    c.py = ty * TILE + (warp >> 1) * 4 + (lane >> 3);
-    c.inside = c.px < V.width && c.py < V.height;
-    c.pix = V.pixel_base + (int64_t)c.py * V.width + c.px;
-    const float ux = ((float)c.px + 0.5f - V.cx) / V.fx;
-    const float uy = ((float)c.py + 0.5f - V.cy) / V.fy;
-    c.r2 = fmaf(ux, ux, fmaf(uy, uy, 1.0f));
-    c.rlen = sqrtf(c.r2);
-    const int2 rg = ranges[tile];
-    c.start = rg.x;
-    c.end = rg.y;
-    c.rec_base = (int64_t)c.v * P;
-    return c;
-}
 
 __device__ __forceinline__ float load_m0(const Params& p, const void* moments, int64_t pix) {
     return reinterpret_cast<const float*>(moments)[pix];   // m0 is the first plane in every storage format
@@ -91,114 +32,130 @@ __device__ __forceinline__ void flush_batch(const float* s_acc, int nb, int nf, 
 // derivatives go through the record geometry to the per-record gradients;
 // the bound derivatives sum into the pixel's Phi, written out as the moment
 // adjoint polynomial psi.
-template <int NI>
+template <int NI, bool SAVED>
 __global__ void __launch_bounds__(TPB, 2)
-    k_bwd_quadrature(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
-                     const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
-                     const float* __restrict__ recon, const void* __restrict__ moments,
+    k_bwd_quadrature(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
+                     const int32_t* __restrict__ ids, const int2* __restrict__ ranges, int64_t P, int64_t npix,
+                     const StatusWords* sw, const float* __restrict__ recon, const void* __restrict__ moments,
                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
-                     const float* __restrict__ dL_dP, float* __restrict__ psi_out, float* __restrict__ grec) {
+                     const float* __restrict__ dL_dP, float* __restrict__ psi_out, float* __restrict__ grec,
+                     const int* __restrict__ pq_off, const float4* __restrict__ pq, int64_t qcap) {
     extern __shared__ float4 s_raw[];
+    __shared__ int s_slot;
     float* s_rec = reinterpret_cast<float*>(s_raw);
-    float* s_acc = s_rec + REC * TPB;                 // [TPB][NGRAD]
-    BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
-    if (sw->n_valid == 0) c.end = c.start;
-    Recon R;
-    PixelAdj pa;
-    float B[NB];
-#pragma unroll
-    for (int k = 0; k < NB; ++k) B[k] = 0.0f;
-    if (c.inside) {
-        R = load_recon(recon, npix, c.pix);
-        const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
-        const float O = saved[3 * npix + c.pix];
-        const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
-        pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
-    }
+    float* s_acc = s_rec + REC * p.batch;             // [batch][NGRAD]
+    // saved queries exist only when the frame's pixel pairs fit the capacity
+    // (the status word then carries MB3DGS_ERR_CAPACITY)
+    const bool any = sw->n_valid != 0 && !(SAVED && sw->n_pixpairs > (unsigned long long)qcap);
+    const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
     const int lane = threadIdx.x & 31;
-    const int n = c.end - c.start;
-    const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-    for (int b = 0; b * TPB < n; ++b) {
-        for (int q = threadIdx.x; q < TPB * NGRAD; q += TPB) s_acc[q] = 0.0f;
-        const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
-        for (int k = 0; k < nb; ++k) {
-            const float* r = s_rec + k * REC;
-            const bool active = c.inside && rect_contains(r, c.px, c.py);
-            if (!__any_sync(0xffffffffu, active)) continue;
-            float acc[32];
+    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
+        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
+        if (!any) c.end = c.start;
+        const float4* qp = nullptr;
+        Recon R;
+        PixelAdj pa;
+        float B[NB];
 #pragma unroll
-            for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
-            if (active) {
-                const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
-                const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
-                const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
-                const PairOut po = pair_backward<NI>(p, R, g, a, pa.gP, B);
-                geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, po.g_mu, po.g_Sig, po.g_what, acc);
-                acc[G_RGB + 0] = pa.gS[0] * po.O;
-                acc[G_RGB + 1] = pa.gS[1] * po.O;
-                acc[G_RGB + 2] = pa.gS[2] * po.O;
-            }
-            const float v = reduce_scatter32(acc);
-            if (lane < NGRAD && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+        for (int k = 0; k < NB; ++k) B[k] = 0.0f;
+        if (c.inside) {
+            R = load_recon(recon, npix, c.pix);
+            const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
+            const float O = saved[3 * npix + c.pix];
+            const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
+            pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
+            if (SAVED) qp = pq + (size_t)pq_off[c.pix] * nq;
         }
-        __syncthreads();
-        flush_batch(s_acc, nb, NGRAD, ids, c.start + b * TPB, c.rec_base, grec);
-        __syncthreads();
-    }
-    if (!c.inside) return;
-    float psi[NPOLY];
-    phi_monomials(R, B, psi);
-    finish_moment_adjoint(p, R, pa.gm0, psi);
+        const int n = c.end - c.start;
+        const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
+        for (int b = 0; b * p.batch < n; ++b) {
+            for (int q = threadIdx.x; q < p.batch * NGRAD; q += TPB) s_acc[q] = 0.0f;
+            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
+            for (int k = 0; k < nb; ++k) {
+                const float* r = s_rec + k * REC;
+                const bool active = c.inside && rect_contains(r, c.px, c.py);
+                if (!__any_sync(0xffffffffu, active)) continue;
+                float acc[32];
 #pragma unroll
-    for (int k = 0; k < NPOLY; ++k) psi_out[k * npix + c.pix] = psi[k];
+                for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
+                if (active) {
+                    const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
+                    const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
+                    const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
+                    const PairOut po = pair_backward<NI, SAVED>(p, R, g, a, pa.gP, B, qp);
+                    if (SAVED) qp += nq;
+                    geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, po.g_mu, po.g_Sig, po.g_what, acc);
+                    acc[G_RGB + 0] = pa.gS[0] * po.O;
+                    acc[G_RGB + 1] = pa.gS[1] * po.O;
+                    acc[G_RGB + 2] = pa.gS[2] * po.O;
+                }
+                const float v = reduce_scatter32(acc);
+                if (lane < NGRAD && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+            }
+            __syncthreads();
+            flush_batch(s_acc, nb, NGRAD, ids, c.start + b * p.batch, c.rec_base, grec);
+            __syncthreads();
+        }
+        if (c.inside) {
+            float psi[NPOLY];
+            phi_monomials(R, B, psi);
+            finish_moment_adjoint(p, R, pa.gm0, psi);
+#pragma unroll
+            for (int k = 0; k < NPOLY; ++k) psi_out[k * npix + c.pix] = psi[k];
+        }
+    }
 }
 
 // ---------------------------------------------------------------- pass 2
 // Per pair: int psi d(d mu_i) through the reverse sweep of the moment
 // recurrence, chained to the record geometry (fields before G_RGB).
 __global__ void __launch_bounds__(TPB, 3)
-    k_bwd_moments(Params p, ViewTable vt, const float* __restrict__ rec, const int32_t* __restrict__ ids,
-                  const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWordsB* sw,
+    k_bwd_moments(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec, const int32_t* __restrict__ ids,
+                  const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWords* sw,
                   const float* __restrict__ recon, const float* __restrict__ psi_in, float* __restrict__ grec) {
     extern __shared__ float4 s_raw[];
+    __shared__ int s_slot;
     float* s_rec = reinterpret_cast<float*>(s_raw);
-    float* s_acc = s_rec + REC * TPB;                 // [TPB][NGRAD]
-    BwdPixel c = bwd_pixel(vt, ranges, P, blockIdx.x);
-    if (sw->n_valid == 0) c.end = c.start;
-    Recon R;                                          // only the standardisation (c, 1/s) is used
-    float psi[NPOLY];
-    if (c.inside) {
-        R.c = recon[1 * npix + c.pix];
-        R.inv_s = recon[2 * npix + c.pix];
-#pragma unroll
-        for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
-    }
+    float* s_acc = s_rec + REC * p.batch;             // [batch][NGRAD]
+    const bool any = sw->n_valid != 0;
     const int lane = threadIdx.x & 31;
-    const int n = c.end - c.start;
-    const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-    for (int b = 0; b * TPB < n; ++b) {
-        for (int q = threadIdx.x; q < TPB * NGRAD; q += TPB) s_acc[q] = 0.0f;
-        const int nb = stage_batch_b(s_rec, rec, ids, c.rec_base, c.start, c.end, b);
-        for (int k = 0; k < nb; ++k) {
-            const float* r = s_rec + k * REC;
-            const bool active = c.inside && rect_contains(r, c.px, c.py);
-            if (!__any_sync(0xffffffffu, active)) continue;
-            float acc[32];
+    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
+        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
+        if (!any) c.end = c.start;
+        Recon R;                                      // only the standardisation (c, 1/s) is used
+        float psi[NPOLY];
+        if (c.inside) {
+            R.c = recon[1 * npix + c.pix];
+            R.inv_s = recon[2 * npix + c.pix];
 #pragma unroll
-            for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
-            if (active) {
-                const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
-                const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
-                float g_mu = 0.0f, g_Sig = 0.0f, g_what = 0.0f;
-                moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
-                geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, g_mu, g_Sig, g_what, acc);
-            }
-            const float v = reduce_scatter32(acc);
-            if (lane < G_RGB && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+            for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
         }
-        __syncthreads();
-        flush_batch(s_acc, nb, G_RGB, ids, c.start + b * TPB, c.rec_base, grec);
-        __syncthreads();
+        const int n = c.end - c.start;
+        const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
+        for (int b = 0; b * p.batch < n; ++b) {
+            for (int q = threadIdx.x; q < p.batch * NGRAD; q += TPB) s_acc[q] = 0.0f;
+            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
+            for (int k = 0; k < nb; ++k) {
+                const float* r = s_rec + k * REC;
+                const bool active = c.inside && rect_contains(r, c.px, c.py);
+                if (!__any_sync(0xffffffffu, active)) continue;
+                float acc[32];
+#pragma unroll
+                for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
+                if (active) {
+                    const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
+                    const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
+                    float g_mu = 0.0f, g_Sig = 0.0f, g_what = 0.0f;
+                    moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
+                    geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, g_mu, g_Sig, g_what, acc);
+                }
+                const float v = reduce_scatter32(acc);
+                if (lane < G_RGB && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+            }
+            __syncthreads();
+            flush_batch(s_acc, nb, G_RGB, ids, c.start + b * p.batch, c.rec_base, grec);
+            __syncthreads();
+        }
     }
 }
 
@@ -357,37 +314,54 @@ __global__ void k_preprocess_bwd(Params p, ViewTable vt, const float* __restrict
                        d_weights, d_sh);
 }
 
-int launch_backward(const Params& p, const ViewTable& vt, const Layout& L, char* ws, const mb3dgs_gaussians& g,
-                    const float* dL_drgb, const float* dL_dP, const mb3dgs_gaussian_grads& gr, cudaStream_t st) {
-    if (!gr.means || !gr.scales || !gr.quats || !gr.weights || !gr.sh) return MB3DGS_ERR_INVALID_ARG;
-    const float* rec = reinterpret_cast<const float*>(ws + L.rec);
-    const int32_t* ids = reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]);
-    const int2* ranges = reinterpret_cast<const int2*>(ws + L.ranges);
-    const StatusWordsB* sw = reinterpret_cast<const StatusWordsB*>(ws + L.status);
-    const float* recon = reinterpret_cast<const float*>(ws + L.recon);
-    const float* saved = reinterpret_cast<const float*>(ws + L.saved);
-    float* psi = reinterpret_cast<float*>(ws + L.dm);
+// Pass 1 (zeroes the record gradients first).
+int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layout& L, char* ws,
+                               const float* dL_drgb, const float* dL_dP, cudaStream_t st) {
     float* grec = reinterpret_cast<float*>(ws + L.grec);
     if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
-    if (L.n_tiles > 0) {
-        const size_t smem = sizeof(float) * (REC + NGRAD) * TPB;
-        auto k1 = p.n_intervals == 3 ? k_bwd_quadrature<3> : k_bwd_quadrature<0>;
-        if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaFuncSetAttribute(k_bwd_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return MB3DGS_ERR_CUDA;
-        count_launch();
-        k1<<<(unsigned)L.n_tiles, TPB, smem, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, ws + L.moments,
-                                                   saved, dL_drgb, dL_dP, psi, grec);
-        count_launch();
-        k_bwd_moments<<<(unsigned)L.n_tiles, TPB, smem, st>>>(p, vt, rec, ids, ranges, L.P, L.npix, sw, recon, psi,
-                                                              grec);
-    }
-    if (L.P > 0) {
-        count_launch();
-        k_preprocess_bwd<<<(unsigned)ceil_div64(L.P, 64), 64, 0, st>>>(p, vt, g.means, g.scales, g.quats, g.weights,
-                                                                      g.sh, L.P, g.sh_degree, rec, grec, gr.means,
-                                                                      gr.scales, gr.quats, gr.weights, gr.sh);
-    }
+    if (L.n_tiles == 0) return MB3DGS_OK;
+    const size_t smem = sizeof(float) * (REC + NGRAD) * p.batch;
+    const bool saved_q = L.qcap > 0;
+    auto k1 = p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true> : k_bwd_quadrature<3, false>)
+                                 : (saved_q ? k_bwd_quadrature<0, true> : k_bwd_quadrature<0, false>);
+    if (!allow_dynamic_smem((const void*)k1, sizeof(float) * (REC + NGRAD) * TPB)) return MB3DGS_ERR_CUDA;
+    const TileLaunch t1 = tile_launch(p, L, ws, Q_BWD_QUAD, (const void*)k1, smem, st);
+    count_launch();
+    k1<<<t1.grid, TPB, smem, st>>>(
+        p, vt, t1.ts, reinterpret_cast<const float*>(ws + L.rec),
+        reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
+        L.npix, reinterpret_cast<const StatusWords*>(ws + L.status), reinterpret_cast<const float*>(ws + L.recon),
+        ws + L.moments, reinterpret_cast<const float*>(ws + L.saved), dL_drgb, dL_dP,
+        reinterpret_cast<float*>(ws + L.dm), grec, saved_q ? reinterpret_cast<const int*>(ws + L.pq_off) : nullptr,
+        saved_q ? reinterpret_cast<const float4*>(ws + L.pq) : nullptr, L.qcap);
+    return MB3DGS_OK;
+}
+
+// Pass 2.
+int launch_backward_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
+    if (L.n_tiles == 0) return MB3DGS_OK;
+    const size_t smem = sizeof(float) * (REC + NGRAD) * p.batch;
+    if (!allow_dynamic_smem((const void*)k_bwd_moments, sizeof(float) * (REC + NGRAD) * TPB)) return MB3DGS_ERR_CUDA;
+    const TileLaunch t2 = tile_launch(p, L, ws, Q_BWD_MOM, (const void*)k_bwd_moments, smem, st);
+    count_launch();
+    k_bwd_moments<<<t2.grid, TPB, smem, st>>>(
+        p, vt, t2.ts, reinterpret_cast<const float*>(ws + L.rec),
+        reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
+        L.npix, reinterpret_cast<const StatusWords*>(ws + L.status), reinterpret_cast<const float*>(ws + L.recon),
+        reinterpret_cast<const float*>(ws + L.dm), reinterpret_cast<float*>(ws + L.grec));
+    return MB3DGS_OK;
+}
+
+// Chain rule through the preprocessing to the Gaussian parameters.
+int launch_backward_preprocess(const Params& p, const ViewTable& vt, const Layout& L, char* ws,
+                               const mb3dgs_gaussians& g, const mb3dgs_gaussian_grads& gr, cudaStream_t st) {
+    if (!gr.means || !gr.scales || !gr.quats || !gr.weights || !gr.sh) return MB3DGS_ERR_INVALID_ARG;
+    if (L.P == 0) return MB3DGS_OK;
+    count_launch();
+    k_preprocess_bwd<<<(unsigned)ceil_div64(L.P, 64), 64, 0, st>>>(
+        p, vt, g.means, g.scales, g.quats, g.weights, g.sh, L.P, g.sh_degree,
+        reinterpret_cast<const float*>(ws + L.rec), reinterpret_cast<const float*>(ws + L.grec), gr.means, gr.scales,
+        gr.quats, gr.weights, gr.sh);
     return MB3DGS_OK;
 }
 

@@ -179,8 +179,11 @@ struct PairOut {
 // Recomputes the pair's quadrature (Eq. 7, App. B, App. D) and back-propagates
 // L_i = a O_i + gP P_i: accumulates the bound derivative Phi of the pixel into
 // B and returns the direct derivatives with respect to (mu, Sigma, w-hat).
-template <int NI>
-MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, float a, float gP, float B[NB]) {
+// With SAVED the bound queries come from the quadrature pass (qin, N+1 float4)
+// instead of being solved again.
+template <int NI, bool SAVED = false>
+MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, float a, float gP, float B[NB],
+                            const float4* __restrict__ qin = nullptr) {
     constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
     const int N = NI > 0 ? NI : p.n_intervals;
     float t[NN], tau[NN], gt[NN], gtau[NN], dg[NN];
@@ -197,7 +200,10 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             float gj, dgj;
             warp_g(p, tj, gj, dgj);
             dg[j] = dgj;
-            tau[j] = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q[j]);
+            if (SAVED)
+                tau[j] = unpack_query(qin[j], (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, q[j]);
+            else
+                tau[j] = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q[j]);
             gt[j] = 0.0f;
             gtau[j] = 0.0f;
         }

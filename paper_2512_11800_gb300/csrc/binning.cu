@@ -104,14 +104,6 @@ size_t scan_tmp_elems(int64_t n) {
 }
 
 // ---------------------------------------------------------------- pair emission
-struct StatusWords {
-    int status;
-    int pad;
-    long long n_total;
-    long long n_valid;
-    unsigned long long nonfinite;
-};
-
 __global__ void k_pair_total(const int* __restrict__ counts, const int* __restrict__ offsets, int64_t VP, int64_t cap,
                              StatusWords* sw) {
     long long tot = VP > 0 ? (long long)offsets[VP - 1] + counts[VP - 1] : 0;
@@ -137,8 +129,8 @@ __global__ void k_emit_pairs(ViewTable vt, const float* __restrict__ rec, const 
     const int v = (int)(idx / P);
     const int32_t gi = (int32_t)(idx - (int64_t)v * P);
     const int* ri = reinterpret_cast<const int*>(rec + idx * REC + R_RECT);
-    const int tx0 = ri[0] / TILE, ty0 = ri[1] / TILE, tx1 = ri[2] / TILE, ty1 = ri[3] / TILE;
     const ViewDesc& V = vt.v[v];
+    const int tx0 = ri[0] / V.tile_w, ty0 = ri[1] / V.tile_h, tx1 = ri[2] / V.tile_w, ty1 = ri[3] / V.tile_h;
     int64_t o = offsets[idx];
     if (o < 0 || o + c > cap) {       // never write past the pair arrays
         atomicMin(&sw->status, (int)MB3DGS_ERR_CAPACITY);

@@ -7,20 +7,21 @@
 // bounds L, U (Eq. 8), quadrature (Eq. 7), rescaling (Eq. 15).
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 #include "../../include/mb3dgs.h"
 
 namespace mb {
 
-constexpr int TILE = 16;              // 16x16 pixels per tile, one thread per pixel
-constexpr int TPB = TILE * TILE;      // threads per raster block
+constexpr int TPB = 256;              // threads per raster block: one per pixel of a 256-pixel tile
 constexpr int NMOM = 9;               // 2n+1 moments, n = 4
 constexpr int NQ = 4;                 // n: roots of the kernel polynomial
 constexpr int REC = 32;               // floats per (view, Gaussian) record
 constexpr int RECON = 20;             // floats per pixel of reconstruction state
 constexpr int MAX_NODES = 9;          // N+1 <= 9 sample points
 constexpr int LAG_ITERS = 4;          // Laguerre iterations per root
+constexpr int SCHED_BYTES = 512;      // tile-queue counters and order buckets
 constexpr double OUTER_SPAN = 8.0;   // outer-root search span beyond the Gauss nodes (y units)
 
 // record field offsets (floats)
@@ -48,6 +49,7 @@ struct ViewDesc {
     float fx, fy, cx, cy;
     int width, height;
     int tiles_x, tiles_y;
+    int tile_w, tile_h;  // pixels per tile (tile_w * tile_h = TPB)
     int tile_base;     // first global tile index of this view
     int64_t pixel_base;  // first global pixel index of this view
 };
@@ -60,6 +62,8 @@ struct ViewTable {
 // Method constants passed by value to every kernel.
 struct Params {
     int n_intervals;
+    int batch;        // Gaussian records staged in shared memory at a time (<= TPB)
+    int schedule;     // MB3DGS_SCHEDULE_*
     float kappa, beta, conf_c, t_near, t_far, eps, bias_alpha, m_min, r_mult;
     float bg[3];
     float warp_lambda;
@@ -75,6 +79,17 @@ struct Params {
 };
 
 // Workspace layout (byte offsets), computed on the host.
+// Device status word at the start of every workspace (64 bytes).
+struct StatusWords {
+    int status;                     // MB3DGS_* code (atomicMin of errors)
+    int pad;
+    long long n_total;              // (tile, Gaussian) pairs of the frame
+    long long n_valid;              // pairs written (0 when over capacity)
+    unsigned long long nonfinite;   // Gaussians with non-finite parameters
+    unsigned long long n_pixpairs;  // (pixel, Gaussian) pairs: pixel centre in the proxy rectangle
+};
+static_assert(sizeof(StatusWords) <= 64, "status region");
+
 struct Layout {
     size_t status;      // int32 status; int32 pad; int64 n_pairs_total; int64 n_pairs_valid; int64 n_nonfinite
     size_t rec;         // float [VP][REC]
@@ -89,9 +104,15 @@ struct Layout {
     size_t recon;       // float [RECON][NPIX]
     size_t saved;       // float [4][NPIX]: sum L (3), O
     size_t dm;          // float [9][NPIX] adjoint moments (backward)
-    size_t grec;        // float [VP][16] per-record gradients (backward)
+    size_t grec;        // float [VP][28] per-record gradients (backward)
+    size_t order;       // int32 [T] tiles in work order (longest list first)
+    size_t sched;       // SCHED_BYTES: per-launch tile queues, bucket counts and cursors
+    size_t npp;         // int32 [NPIX] (pixel, Gaussian) pairs per pixel
+    size_t pq_off;      // int32 [NPIX] exclusive scan of npp
+    size_t pq;          // float4 [qcap][N+1] saved bound queries {tau, x0, x1, j | nroot << 4}
     size_t total;
     int64_t VP, P, npix, cap;
+    int64_t qcap;       // query slots (0: queries are recomputed by the backward)
     int64_t n_tiles;
     int nb_sort, sort_passes, final_buf;
     int n_views;
@@ -313,7 +334,7 @@ struct QueryRec {
 // y = 2 eta - 1 (Sec. 3.2, Eq. 8).  REC keeps the roots for the adjoint.
 template <bool REC>
 MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) {
-    if (REC) { rec->nroot = 0; rec->j = 0; rec->F = 0.0f; rec->y = 0.0f; }
+    if (REC) { rec->nroot = 0; rec->j = 0; rec->F = 0.0f; rec->y = 0.0f; rec->x[0] = 0.0f; rec->x[1] = 0.0f; }
     if (R.m0 <= 0.0f) return 0.0f;
     const float y = (y_raw - R.c) * R.inv_s;
     float P[5];
@@ -371,6 +392,40 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
 
 MB_HD float optical_depth(const Recon& R, float beta, float y_raw) {
     return bound_query<false>(R, beta, y_raw, nullptr);
+}
+
+// A bound query kept by the quadrature pass for the adjoint (one float4):
+// {tau, x_0, x_1, j | nroot << 4}; the standardised y is recomputed.
+MB_HD float int_bits_as_float(int i) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(i);
+#else
+    float f;
+    memcpy(&f, &i, 4);
+    return f;
+#endif
+}
+MB_HD int float_bits_as_int(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_int(f);
+#else
+    int i;
+    memcpy(&i, &f, 4);
+    return i;
+#endif
+}
+MB_HD float4 pack_query(float tau, const QueryRec& q) {
+    return make_float4(tau, q.x[0], q.x[1], int_bits_as_float(q.j | (q.nroot << 4)));
+}
+MB_HD float unpack_query(const float4 v, float y, QueryRec& q) {
+    const int m = float_bits_as_int(v.w);
+    q.y = y;
+    q.j = m & 15;
+    q.nroot = m >> 4;
+    q.x[0] = v.y;
+    q.x[1] = v.z;
+    q.F = 0.0f;
+    return v.x;
 }
 
 #ifndef MB_RECON_T
@@ -531,8 +586,9 @@ MB_HD void store_recon(const Recon& R, float* __restrict__ rc, int64_t npix, int
 // NI > 0: compile-time number of intervals; NI == 0: runtime p.n_intervals.
 // Returns O_i; adds P_i to *pen.
 // ----------------------------------------------------------------------------
-template <int NI>
-MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, float* pen) {
+template <int NI, bool SAVE = false>
+MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, float* pen,
+                            float4* __restrict__ qout = nullptr) {
     constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
     const int N = NI > 0 ? NI : p.n_intervals;
     float t[NN], tau[NN];
@@ -543,7 +599,13 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
             float tj = fminf(fmaxf(fmaf(ks, p.x_nodes[j], g.mu), p.t_near), p.t_far);
             t[j] = tj;
             float y = fmaf(2.0f, warp_only(p, tj), -1.0f);
-            tau[j] = optical_depth(R, p.beta, y);
+            if (SAVE && qout) {
+                QueryRec q;
+                tau[j] = bound_query<true>(R, p.beta, y, &q);
+                qout[j] = pack_query(tau[j], q);
+            } else {
+                tau[j] = optical_depth(R, p.beta, y);
+            }
         }
     }
     const float inv2s2 = 0.5f / g.Sig2;
@@ -570,6 +632,15 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
     }
     *pen += P;
     return O;
+}
+
+// Pixel of a thread in a tile: each warp covers an 8 x 4 block (fewer
+// partially covered warps than 32 x 1 rows for rectangle-shaped footprints),
+// warps laid out row-major over the tile.
+MB_HD void tile_pixel(const ViewDesc& V, int tx, int ty, int lane, int warp, int& px, int& py) {
+    const int wpr = V.tile_w >> 3;
+    px = tx * V.tile_w + (warp % wpr) * 8 + (lane & 7);
+    py = ty * V.tile_h + (warp / wpr) * 4 + (lane >> 3);
 }
 
 MB_HD int find_view(const ViewTable& vt, int64_t tile) {

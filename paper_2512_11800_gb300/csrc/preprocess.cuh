@@ -210,7 +210,7 @@ MB_HD void preprocess_one(const Params& p, const ViewDesc& V, const float* __res
     r[R_AY] = (float)ay;
     ri[R_RECT + 0] = x0; ri[R_RECT + 1] = y0; ri[R_RECT + 2] = x1; ri[R_RECT + 3] = y1;
     ri[R_FLAGS] = 1 | (full ? 2 : 0);
-    const int tx0 = x0 / TILE, tx1 = x1 / TILE, ty0 = y0 / TILE, ty1 = y1 / TILE;
+    const int tx0 = x0 / V.tile_w, tx1 = x1 / V.tile_w, ty0 = y0 / V.tile_h, ty1 = y1 / V.tile_h;
     *count = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
 }
 

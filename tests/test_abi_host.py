@@ -57,7 +57,7 @@ def test_workspace_size_and_validation(lib):
     a = n.value
     assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 1000, 1 << 20, C.byref(n)) == 0
     assert n.value >= a + 16 * (1 << 20)            # four 32-bit pair arrays
-    assert lib.mb3dgs_num_tiles(C.byref(cam), 1) == 120 * 68
+    assert lib.mb3dgs_num_tiles(None, C.byref(cam), 1) == 120 * 68
     bad = B.Config()
     lib.mb3dgs_config_default(C.byref(bad))
     bad.n = 3
@@ -78,4 +78,4 @@ def test_workspace_size_and_validation(lib):
 def test_multiview_tiles(lib):
     from paper_2512_11800_gb300 import _binding as B
     cams = (B.Camera * 3)(_cam(640, 360), _cam(1280, 720), _cam(1920, 1080))
-    assert lib.mb3dgs_num_tiles(cams, 3) == 40 * 23 + 80 * 45 + 120 * 68
+    assert lib.mb3dgs_num_tiles(None, cams, 3) == 40 * 23 + 80 * 45 + 120 * 68

@@ -20,12 +20,12 @@ torch.set_num_threads(os.cpu_count() or 8)
 NAMES = ["means", "scales", "quats", "weights", "sh"]
 
 
-@pytest.fixture(scope="module")
-def R():
+@pytest.fixture(scope="module", params=[True, False], ids=["saved_queries", "recomputed_queries"])
+def R(request):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2512_11800_gb300 import RasterConfig, Rasterizer
-    return Rasterizer(RasterConfig(bg=(0.1, 0.2, 0.3)))
+    return Rasterizer(RasterConfig(bg=(0.1, 0.2, 0.3), save_queries=request.param))
 
 
 def G(sc):
@@ -43,6 +43,16 @@ def gpu_grads(R, sc, cam, g_img, gP_img):
     return {k: v.detach().cpu().double().numpy().reshape(-1) for k, v in grads.items()}
 
 
+_ORACLE = {}
+
+
+def oracle_grad(key, *args, **kw):
+    """The oracle gradient, computed once per case for both query modes."""
+    if key not in _ORACLE:
+        _ORACLE[key] = O.render_grad(*args, **kw)
+    return _ORACLE[key]
+
+
 def rel_errors(gg, ref):
     return {k: float(np.linalg.norm(gg[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
 
@@ -53,9 +63,9 @@ def test_backward_uniform2k_full_image(R):
     g_img = rng.normal(size=(cam.height, cam.width, 3))
     gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
     gg = gpu_grads(R, sc, cam, g_img, gP_img)
-    ref = O.render_grad(sc, cam, oracle_config(R.config), g_img, gP_img)
+    ref = oracle_grad("uniform2k", sc, cam, oracle_config(R.config), g_img, gP_img)
     err = rel_errors(gg, ref)
-    print("uniform2k backward rel-L2", err)
+    print("uniform2k backward rel-L2", "saved" if R.config.save_queries else "recomputed", err)
     assert max(err.values()) <= REL, err
 
 
@@ -66,7 +76,7 @@ def test_backward_sh3_near_camera(R):
     g_img = rng.normal(size=(cam.height, cam.width, 3))
     gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
     gg = gpu_grads(R, sc, cam, g_img, gP_img)
-    ref = O.render_grad(sc, cam, oracle_config(R.config), g_img, gP_img)
+    ref = oracle_grad("sh3_near", sc, cam, oracle_config(R.config), g_img, gP_img)
     err = rel_errors(gg, ref)
     assert max(err.values()) <= REL, err
 
@@ -111,3 +121,24 @@ def test_autograd_function_matches_direct_call(R):
     for k, a in zip(NAMES, auto):
         b = direct[k]
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-7), k
+
+
+def test_query_capacity_overflow_is_reported(R):
+    """Fewer query slots than (pixel, Gaussian) pairs: MB3DGS_ERR_CAPACITY in
+    the status word, the forward image unchanged, nothing written out of
+    bounds (the kernels only use saved queries when all pairs fit)."""
+    if not R.config.save_queries:
+        pytest.skip("queries are not saved")
+    sc, cam = scenes.workload("uniform2k_128")
+    g = G(sc)
+    tp, pp = R.pair_counts(g, cam)
+    ref = R.render(g, cam, capacity=tp, query_capacity=pp)
+    rgb_ref = ref["rgb"].clone()
+    assert R.status()[0] == 0
+    out = R.render(g, cam, capacity=tp, query_capacity=pp // 2)
+    assert R.status()[0] == -7
+    assert torch.equal(out["rgb"], rgb_ref)
+    dr = torch.ones_like(out["rgb"])
+    grads = R.backward(g, cam, tp, dr)
+    torch.cuda.synchronize()
+    assert all(torch.isfinite(v).all() for v in grads.values())
