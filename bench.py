@@ -115,6 +115,20 @@ def dist_setup(n_gpus):
     return None, 0, 1
 
 
+def max_over_ranks(dist, ms, device):
+    """The slowest rank's step time (every rank gets it)."""
+    if not dist:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mpix_s(world, pixels_per_rank, ms):
+    """Whole-job throughput of N replicas: all ranks' pixels over the slowest rank's time."""
+    return world * pixels_per_rank / (ms * 1e-3) / 1e6
+
+
 def oracle_step(sc, cam, size, with_bwd, target):
     """One oracle step on a centred size x size crop: forward, or forward +
     gradient of the L2 loss against the target crop (autograd in FP64)."""
@@ -282,10 +296,7 @@ def run_single(args, dist, rank, world, dev):
     clk = clocks.stop()
     ms = t_start.elapsed_time(t_end) / args.steps
     stage_ms = {name: statistics.median(e[i].elapsed_time(e[i + 1]) for e in evs) for i, name in enumerate(STAGES)}
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, ms, dev)
     st, tile_pairs, pairs = pair_counts(R, fr)
 
     # end to end through the public API: pinned host inputs -> device, render,
@@ -330,7 +341,7 @@ def run_single(args, dist, rank, world, dev):
     dom_ms = stage_ms["bwd_quadrature" if dominant == "k_bwd_quadrature" else "shade"]
     line = dict(
         metric=METRIC,
-        value=world * npix / (ms * 1e-3) / 1e6,
+        value=job_mpix_s(world, npix, ms),
         unit="Mpixel/s",
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
@@ -403,22 +414,51 @@ def run_batch16(args, dist, rank, world, dev):
     R._ws = None
     torch.cuda.empty_cache()
 
-    # batched: all views in one frame, the step captured in a CUDA graph
-    fb = Frame(R, g, cams, target)
+    # batched: the views packed in order into groups whose saved bound queries
+    # fit the query budget (one group = one set of persistent launches over
+    # all its views' tiles), the whole step captured in one CUDA graph
+    limit = min(2 ** 31 - 1, int(R.config.query_budget_gb * 2 ** 30) // (16 * (R.config.n_intervals + 1)))
+    counts = [R.pair_counts(g, c) for c in cams]
+    groups, cur, cur_pp = [], [], 0
+    for i, (tp, pp) in enumerate(counts):
+        if cur and cur_pp + pp > limit:
+            groups.append(cur)
+            cur, cur_pp = [], 0
+        cur.append(i)
+        cur_pp += pp
+    groups.append(cur)
+    need = 0
+    for grp in groups:
+        gc = [cams[i] for i in grp]
+        tp, pp = R.pair_counts(g, gc)
+        R.set_query_capacity(pp)
+        need = max(need, R.workspace_bytes(gc, g.P, tp))
+    R._ws = None
+    shared = R.workspace(need)
+    fbs = [Frame(R, g, [cams[i] for i in grp], target[offs[grp[0]]:offs[grp[-1] + 1]], ws=shared)
+           for grp in groups]
+
+    def batch_step(st):
+        for f in fbs:
+            f.step(st, with_bwd)
+
     side = torch.cuda.Stream()
     side.wait_stream(stream)
     with torch.cuda.stream(side):
         for _ in range(args.warmup):
-            fb.step(side, with_bwd)
+            batch_step(side)
     stream.wait_stream(side)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     l0 = R.lib.mb3dgs_launch_count()
     with torch.cuda.graph(graph):
-        fb.step(torch.cuda.current_stream(), with_bwd)
+        batch_step(torch.cuda.current_stream())
     launches = R.lib.mb3dgs_launch_count() - l0
     for _ in range(2):
         graph.replay()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler()
     clocks.start()
@@ -428,8 +468,10 @@ def run_batch16(args, dist, rank, world, dev):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    st, tile_pairs, pairs = pair_counts(R, fb)
+    ms = max_over_ranks(dist, e0.elapsed_time(e1) / args.steps, dev)
+    st = max((pair_counts(R, f)[0] for f in fbs), key=abs)
+    tile_pairs = sum(c[0] for c in counts)
+    pairs = sum(c[1] for c in counts)
 
     # end to end: inputs from pinned host memory into the graph's input
     # buffers, replay, rgb back to host
@@ -441,7 +483,10 @@ def run_batch16(args, dist, rank, world, dev):
         for k in host:
             getattr(g, k).copy_(host[k], non_blocking=True)
         graph.replay()
-        rgb_host.copy_(fb.rgb, non_blocking=True)
+        o = 0
+        for f in fbs:
+            rgb_host[o:o + f.rgb.shape[0]].copy_(f.rgb, non_blocking=True)
+            o += f.rgb.shape[0]
 
     e2e_step()
     torch.cuda.synchronize()
@@ -456,15 +501,16 @@ def run_batch16(args, dist, rank, world, dev):
     tot = sum(npix)
     return dict(
         metric=METRIC,
-        value=world * tot / (ms * 1e-3) / 1e6,
+        value=job_mpix_s(world, tot, ms),
         unit="Mpixel/s",
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
         config={"workload": "batch16_shells1M", "gaussians": g.P, "views": [[c.width, c.height] for c in cams],
                 "pixels": tot, "pass": "forward+backward" if with_bwd else "forward",
-                "saved_queries": fb.qcap > 0,
+                "saved_queries": all(f.qcap > 0 for f in fbs), "groups": groups,
                 "tiling": dict(tile=list(tuned[:2]), batch=tuned[2], schedule=tuned[3], tuned_ms=tuned[4]),
-                "graph": "whole step in one CUDA graph", "l2": "inputs larger than L2",
+                "graph": "whole step in one CUDA graph (one set of persistent launches per view group)",
+                "l2": "inputs larger than L2",
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         sequential=dict(ms_per_step=seq_ms, mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
                         how="16 x (render + backward) single-view eager calls"),

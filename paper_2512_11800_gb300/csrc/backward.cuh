@@ -181,33 +181,44 @@ struct PairOut {
 // B and returns the direct derivatives with respect to (mu, Sigma, w-hat).
 // With SAVED the bound queries come from the quadrature pass (qin, N+1 float4)
 // instead of being solved again.
+// One sample t_j of a pair with its bound query and running adjoints.
+struct Sample {
+    float t, tau, dg, b, erf;   // sample, optical depth, warp slope, (t - mu)/(sqrt2 Sigma), erf(b)
+    bool clamped;               // t_j clamped to [t_n, t_f] (no derivative to mu, Sigma)
+    QueryRec q;
+    float gt, gtau;             // dL/dt_j, dL/dtau_j
+};
+
+template <bool SAVED>
+MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float isq, int j,
+                       const float4* __restrict__ qin, Sample& s) {
+    const float raw = fmaf(p.kappa * g.Sig, p.x_nodes[j], g.mu);
+    s.t = fminf(fmaxf(raw, p.t_near), p.t_far);
+    s.clamped = s.t != raw;
+    float gj;
+    warp_g(p, s.t, gj, s.dg);
+    if (SAVED)
+        s.tau = unpack_query(qin[j], (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, s.q);
+    else
+        s.tau = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &s.q);
+    s.b = (s.t - g.mu) * isq;
+    s.erf = erff(s.b);
+    s.gt = 0.0f;
+    s.gtau = 0.0f;
+}
+
+// Recomputes the pair's quadrature (Eq. 7, App. B, App. D) and back-propagates
+// L_i = a O_i + gP P_i: accumulates the bound derivative Phi of the pixel into
+// B and returns the direct derivatives with respect to (mu, Sigma, w-hat).
+// With SAVED the bound queries come from the quadrature pass (qin, N+1 float4)
+// instead of being solved again.  Streamed over the samples: interval j is
+// processed once samples j and j+1 are loaded, after which sample j's
+// adjoints are final and go through its bound query (one copy of the query
+// code, no per-sample arrays).
 template <int NI, bool SAVED = false>
 MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, float a, float gP, float B[NB],
                             const float4* __restrict__ qin = nullptr) {
-    constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
     const int N = NI > 0 ? NI : p.n_intervals;
-    float t[NN], tau[NN], gt[NN], gtau[NN], dg[NN];
-    bool clampd[NN];
-    QueryRec q[NN];
-    const float ks = p.kappa * g.Sig;
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-        if (NI > 0 || j <= N) {
-            const float raw = fmaf(ks, p.x_nodes[j], g.mu);
-            const float tj = fminf(fmaxf(raw, p.t_near), p.t_far);
-            clampd[j] = tj != raw;
-            t[j] = tj;
-            float gj, dgj;
-            warp_g(p, tj, gj, dgj);
-            dg[j] = dgj;
-            if (SAVED)
-                tau[j] = unpack_query(qin[j], (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, q[j]);
-            else
-                tau[j] = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q[j]);
-            gt[j] = 0.0f;
-            gtau[j] = 0.0f;
-        }
-    }
     PairOut o;
     o.O = 0.0f;
     o.g_mu = 0.0f;
@@ -217,18 +228,21 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
     const float isq = 0.70710678118654752f / g.Sig;
     const float tscale = g.what * g.Sig * 1.25331413731550025f;
     const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
-    float b_prev = (t[0] - g.mu) * isq;
-    float erf_prev = erff(b_prev);
-#pragma unroll
-    for (int j = 0; j < NN - 1; ++j) {
-        if (NI > 0 || j < N) {
-            const float Delta = t[j + 1] - t[j];
-            const float dtr = tau[j + 1] - tau[j];
+    Sample c, n;
+    load_sample<SAVED>(p, R, g, isq, 0, qin, c);
+#pragma unroll 1
+    for (int j = 0; j <= N; ++j) {
+        if (j < N) {
+            load_sample<SAVED>(p, R, g, isq, j + 1, qin, n);
+            // interval j: term = T_j ph(dtau) sig_j Delta_j and the penalty v^2
+            const float Delta = n.t - c.t;
+            const float dtr = n.tau - c.tau;
             const bool pos = dtr > 0.0f;
             const float dtau = pos ? dtr : 0.0f;
-            const float Tj = expf(-tau[j]);
-            const float d0 = t[j] - g.mu;
-            const float sig = g.what * expf(-d0 * d0 * inv2s2);
+            const float Tj = expf(-c.tau);
+            const float d0 = c.t - g.mu;
+            const float e0 = expf(-d0 * d0 * inv2s2);
+            const float sig = g.what * e0;
             float ph, dph;
             if (dtau < 1e-4f) {
                 ph = fmaf(dtau, fmaf(dtau, 1.0f / 6.0f, -0.5f), 1.0f);
@@ -240,55 +254,44 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             }
             const float term = Tj * ph * sig * Delta;
             o.O += term;
-            const float b_next = (t[j + 1] - g.mu) * isq;
-            const float erf_next = erff(b_next);
-            const float tij = tscale * (erf_next - erf_prev);
+            const float tij = tscale * (n.erf - c.erf);
             const float v = fmaxf(tij - dtau, 0.0f);
-            // adjoints of term = T_j ph(dtau) sig_j Delta_j and v^2
-            gtau[j] -= a * term;
+            c.gtau -= a * term;
             const float gdt = a * Tj * dph * sig * Delta - 2.0f * gP * v;
             if (pos) {
-                gtau[j + 1] += gdt;
-                gtau[j] -= gdt;
+                n.gtau += gdt;
+                c.gtau -= gdt;
             }
-            {
-                const float gsig = a * Tj * ph * Delta;
-                const float gD = a * Tj * ph * sig;
-                gt[j + 1] += gD;
-                gt[j] -= gD;
-                const float sd = gsig * sig * d0 / g.Sig2;
-                gt[j] -= sd;
-                o.g_mu += sd;
-                o.g_Sig += sd * d0 / g.Sig;
-                o.g_what += gsig * expf(-d0 * d0 * inv2s2);
-                const float gtij = 2.0f * gP * v;
-                if (gtij != 0.0f) {
-                    o.g_what += gtij * tscale * (erf_next - erf_prev) / fmaxf(g.what, 1e-30f);
-                    o.g_Sig += gtij * tij / g.Sig;
-                    const float c1 = gtij * dscale * expf(-b_next * b_next);
-                    const float c0 = -gtij * dscale * expf(-b_prev * b_prev);
-                    gt[j + 1] += c1 * isq;
-                    gt[j] += c0 * isq;
-                    o.g_mu -= (c1 + c0) * isq;
-                    o.g_Sig -= (c1 * b_next + c0 * b_prev) / g.Sig;
-                }
-            }
-            b_prev = b_next;
-            erf_prev = erf_next;
-        }
-    }
-    // through the bound queries
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-        if (NI > 0 || j <= N) {
-            float gy = 0.0f;
-            query_adjoint(p, R, q[j], gtau[j], &gy, B);
-            gt[j] = fmaf(gy, 2.0f * dg[j] * R.inv_s, gt[j]);
-            if (!clampd[j]) {
-                o.g_mu += gt[j];
-                o.g_Sig = fmaf(gt[j], p.kappa * p.x_nodes[j], o.g_Sig);
+            const float gsig = a * Tj * ph * Delta;
+            const float gD = a * Tj * ph * sig;
+            n.gt += gD;
+            c.gt -= gD;
+            const float sd = gsig * sig * d0 / g.Sig2;
+            c.gt -= sd;
+            o.g_mu += sd;
+            o.g_Sig += sd * d0 / g.Sig;
+            o.g_what += gsig * e0;
+            const float gtij = 2.0f * gP * v;
+            if (gtij != 0.0f) {
+                o.g_what += gtij * tscale * (n.erf - c.erf) / fmaxf(g.what, 1e-30f);
+                o.g_Sig += gtij * tij / g.Sig;
+                const float c1 = gtij * dscale * expf(-n.b * n.b);
+                const float c0 = -gtij * dscale * expf(-c.b * c.b);
+                n.gt += c1 * isq;
+                c.gt += c0 * isq;
+                o.g_mu -= (c1 + c0) * isq;
+                o.g_Sig -= (c1 * n.b + c0 * c.b) / g.Sig;
             }
         }
+        // sample j is final: through its bound query to y_j and the moments
+        float gy = 0.0f;
+        query_adjoint(p, R, c.q, c.gtau, &gy, B);
+        c.gt = fmaf(gy, 2.0f * c.dg * R.inv_s, c.gt);
+        if (!c.clamped) {
+            o.g_mu += c.gt;
+            o.g_Sig = fmaf(c.gt, p.kappa * p.x_nodes[j], o.g_Sig);
+        }
+        c = n;
     }
     return o;
 }

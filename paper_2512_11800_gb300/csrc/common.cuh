@@ -359,29 +359,34 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
     } else if (j == NQ) {
         L = 1.0f - w0;
     } else {
-        float acc = 0.0f;
-        // outer root: left of z_1 (j <= 2) or right of z_4 (j == 3)
         const bool left = (j <= 2);
         const float zb = left ? R.z[0] : R.z[3];
         const float far = left ? zb - R.span : zb + R.span;
         const float ff = kernel_poly(R, e, far);
         const float fz = kernel_poly(R, e, zb);
-        if ((ff > 0.0f) != (fz > 0.0f)) {
-            float x = left ? laguerre(R, e, far, far, zb, true) : laguerre(R, e, far, zb, far, false);
-            acc += christoffel_weight(R, x);
-            if (REC) { rec->x[0] = x; rec->nroot = 1; }
-        }
-        if (j == 2) {
-            // interior root in (z_1, z_2), approached from z_2 (next to eta's interval)
-            float x = laguerre(R, e, R.z[1], R.z[0], R.z[1], false);
+        const bool outer = (ff > 0.0f) != (fz > 0.0f);
+        const bool inner = j == 2;
+        const int ns = (int)outer + (int)inner;
+        float acc = 0.0f;
+        // At most two root solves, through one copy of the solver so that
+        // lanes needing one root of either kind iterate together: first the
+        // interior root in (z_1, z_2) approached from z_2 (next to eta's
+        // interval) when j == 2, then the outer root left of z_1 (j <= 2) or
+        // right of z_4 (j == 3) when K changes sign beyond the nodes.
+#pragma unroll 1
+        for (int sv = 0; sv < ns; ++sv) {
+            const bool in = inner && sv == 0;
+            const float x0 = in ? R.z[1] : far;
+            const float lo = in ? R.z[0] : (left ? far : zb);
+            const float hi = in ? R.z[1] : (left ? zb : far);
+            const float x = laguerre(R, e, x0, lo, hi, !in && left);
             acc += christoffel_weight(R, x);
             if (REC) {   // static indices keep the record in registers
-                const bool second = rec->nroot > 0;
-                rec->x[1] = second ? x : rec->x[1];
-                rec->x[0] = second ? rec->x[0] : x;
-                rec->nroot += 1;
+                if (sv == 0) rec->x[0] = x;
+                else rec->x[1] = x;
             }
         }
+        if (REC) rec->nroot = ns;
         L = left ? acc : 1.0f - w0 - acc;
     }
     L = fminf(fmaxf(L, 0.0f), 1.0f - w0);
@@ -589,46 +594,43 @@ MB_HD void store_recon(const Recon& R, float* __restrict__ rc, int64_t npix, int
 template <int NI, bool SAVE = false>
 MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, float* pen,
                             float4* __restrict__ qout = nullptr) {
-    constexpr int NN = NI > 0 ? NI + 1 : MAX_NODES;
+    // streamed over the samples (one copy of the bound-query code): interval
+    // j-1 is accumulated once sample j is known
     const int N = NI > 0 ? NI : p.n_intervals;
-    float t[NN], tau[NN];
     const float ks = p.kappa * g.Sig;
-#pragma unroll
-    for (int j = 0; j < NN; ++j) {
-        if (NI > 0 || j <= N) {
-            float tj = fminf(fmaxf(fmaf(ks, p.x_nodes[j], g.mu), p.t_near), p.t_far);
-            t[j] = tj;
-            float y = fmaf(2.0f, warp_only(p, tj), -1.0f);
-            if (SAVE && qout) {
-                QueryRec q;
-                tau[j] = bound_query<true>(R, p.beta, y, &q);
-                qout[j] = pack_query(tau[j], q);
-            } else {
-                tau[j] = optical_depth(R, p.beta, y);
-            }
-        }
-    }
     const float inv2s2 = 0.5f / g.Sig2;
     const float isq = 0.70710678118654752f / g.Sig;
     const float tscale = g.what * g.Sig * 1.25331413731550025f;
     float O = 0.0f, P = 0.0f;
-    float erf_prev = erff((t[0] - g.mu) * isq);
-#pragma unroll
-    for (int j = 0; j < NN - 1; ++j) {
-        if (NI > 0 || j < N) {
-            const float Delta = t[j + 1] - t[j];
-            const float dtau = fmaxf(tau[j + 1] - tau[j], 0.0f);
-            const float Tj = expf(-tau[j]);
-            const float dt0 = t[j] - g.mu;
+    float t_prev = 0.0f, tau_prev = 0.0f, erf_prev = 0.0f;
+#pragma unroll 1
+    for (int j = 0; j <= N; ++j) {
+        const float tj = fminf(fmaxf(fmaf(ks, p.x_nodes[j], g.mu), p.t_near), p.t_far);
+        const float y = fmaf(2.0f, warp_only(p, tj), -1.0f);
+        float tau;
+        if (SAVE && qout) {
+            QueryRec q;
+            tau = bound_query<true>(R, p.beta, y, &q);
+            qout[j] = pack_query(tau, q);
+        } else {
+            tau = optical_depth(R, p.beta, y);
+        }
+        const float erf_j = erff((tj - g.mu) * isq);
+        if (j > 0) {
+            const float Delta = tj - t_prev;
+            const float dtau = fmaxf(tau - tau_prev, 0.0f);
+            const float Tj = expf(-tau_prev);
+            const float dt0 = t_prev - g.mu;
             const float sig = g.what * expf(-dt0 * dt0 * inv2s2);
             const float ratio = dtau < 1e-6f ? fmaf(-0.5f, dtau, 1.0f) : -expm1f(-dtau) / dtau;
             O = fmaf(Tj * ratio, sig * Delta, O);
-            const float erf_next = erff((t[j + 1] - g.mu) * isq);
-            const float tij = tscale * (erf_next - erf_prev);
+            const float tij = tscale * (erf_j - erf_prev);
             const float v = fmaxf(tij - dtau, 0.0f);
             P = fmaf(v, v, P);
-            erf_prev = erf_next;
         }
+        t_prev = tj;
+        tau_prev = tau;
+        erf_prev = erf_j;
     }
     *pen += P;
     return O;
