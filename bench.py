@@ -48,8 +48,14 @@ FP32_LANES_PER_SM = 128
 # workload divided by its pixel pairs).  The ALU roofline of a kernel is
 # this work over its time against the FP32 peak.
 FP32_FLOPS_PER_PAIR = {
-    "k_shade": 1854.0,
-    "k_bwd_quadrature": 2600.0,
+    "k_shade": 1524.0,
+    "k_bwd_quadrature": 1663.0,      # with saved bound queries
+}
+# Thread instructions per pair from the same captures (issue-rate view:
+# peak = SMs x 4 schedulers x 32 lanes x clock).
+THREAD_INST_PER_PAIR = {
+    "k_shade": 1969.0,
+    "k_bwd_quadrature": 1982.0,
 }
 
 
@@ -145,7 +151,7 @@ def oracle_step(sc, cam, size, with_bwd, target):
     return O.render_grad(sc, cam, cfg, g, None, region=region)["out"]["n_pairs"]
 
 
-def cpu_oracle_sample(sc, cam, with_bwd, size=32):
+def cpu_oracle_sample(sc, cam, with_bwd, size=32, name=WORKLOAD):
     """Time the FP64 oracle on a centred crop of the same workload (bounded sample)."""
     torch.set_num_threads(os.cpu_count() or 1)
     target = scenes.target_image(cam.height, cam.width)
@@ -153,8 +159,9 @@ def cpu_oracle_sample(sc, cam, with_bwd, size=32):
     n_pairs = oracle_step(sc, cam, size, with_bwd, target)
     dt = time.perf_counter() - t0
     return dict(value=size * size / dt / 1e6, unit="Mpixel/s", cores=torch.get_num_threads(), kind="oracle",
-                sample="centre %dx%d crop of the 1920x1080 frame of %s (%d pixel pairs), %s, %.1f s" %
-                       (size, size, WORKLOAD, n_pairs, "forward+backward" if with_bwd else "forward", dt))
+                sample="centre %dx%d crop of the %dx%d frame of %s (%d pixel pairs), %s, %.1f s" %
+                       (size, size, cam.width, cam.height, name, n_pairs,
+                        "forward+backward" if with_bwd else "forward", dt))
 
 
 def run_reference(args):
@@ -188,19 +195,23 @@ def run_reference(args):
 def roofline(kernel, ms, pairs, sm_max):
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the max SM clock
     achieved = FP32_FLOPS_PER_PAIR[kernel] * pairs / (ms * 1e-3) / 1e12
+    issue_peak = SM_COUNT * 4 * 32 * sm_max * 1e6                          # thread instructions / s
+    issue = THREAD_INST_PER_PAIR[kernel] * pairs / (ms * 1e-3)
     return dict(kernel=kernel, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=None, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel],
+                traffic=None, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel], issue_frac=issue / issue_peak,
                 peak_note="FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock); executed FP32 flops per pixel "
-                          "pair from ncu opcode counts" % (SM_COUNT, FP32_LANES_PER_SM, sm_max))
+                          "pair from ncu opcode counts; issue_frac = thread instructions per pair x pairs / time over "
+                          "%d SMs x 4 schedulers x 32 lanes x clock" % (SM_COUNT, FP32_LANES_PER_SM, sm_max, SM_COUNT))
 
 
 class Frame:
     """Device buffers and the C-ABI stage calls of one frame (one or more views)."""
 
-    def __init__(self, R, g, cams, target, ws=None):
+    def __init__(self, R, g, cams, target, ws=None, save_queries=True):
         from paper_2512_11800_gb300 import _binding as B
         self.B, self.R, self.g, self.cams = B, R, g, cams
         self.cap, qcap = R.pair_counts(g, cams)
+        qcap = qcap if save_queries else 0      # a forward-only step keeps no queries
         self.qcap = R.set_query_capacity(qcap)
         nbytes = R.workspace_bytes(cams, g.P, self.cap)
         if ws is not None:          # a shared workspace (frames run one after the other)
@@ -268,14 +279,14 @@ def pair_counts(R, frame):
 
 def run_single(args, dist, rank, world, dev):
     from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
-    sc, cam = scenes.workload(WORKLOAD)
+    sc, cam = scenes.workload(args.workload)
     npix = cam.width * cam.height
     R = Rasterizer(RasterConfig(), device=dev)
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
-    fr = Frame(R, g, cam, target)
-    stream = torch.cuda.current_stream()
     with_bwd = not args.forward_only
+    fr = Frame(R, g, cam, target, save_queries=with_bwd)
+    stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         fr.step(stream, with_bwd)
     torch.cuda.synchronize()
@@ -346,13 +357,15 @@ def run_single(args, dist, rank, world, dev):
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
         fwd_mpix_s=world * npix / (fwd_ms * 1e-3) / 1e6,
-        config={"workload": WORKLOAD, "gaussians": g.P, "width": cam.width, "height": cam.height, "sh_degree": 3,
+        config={"workload": args.workload, "gaussians": g.P, "width": cam.width, "height": cam.height,
+                "sh_degree": sc.sh_degree,
                 "n_moments": 9, "n_intervals": 3,
                 "pass": "forward+backward (L2 loss vs random target)" if with_bwd else "forward",
                 "saved_queries": fr.qcap > 0,
                 "tiling": dict(tile=[R.config.tile_w, R.config.tile_h], batch=R.config.batch,
                                schedule=R.config.schedule),
-                "l2": "inputs larger than L2 (236 MB Gaussian parameters + 128 MB records per step)",
+                "l2": "inputs larger than L2 (236 MB Gaussian parameters + 128 MB records per step)"
+                      if args.workload == WORKLOAD else "see workload",
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         stage_ms=stage_ms,
         pairs=pairs, tile_pairs=tile_pairs, status=st,
@@ -364,7 +377,7 @@ def run_single(args, dist, rank, world, dev):
         clocks=clk,
     )
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(sc, cam, with_bwd)
+        line["cpu_baseline"] = cpu_oracle_sample(sc, cam, with_bwd, name=args.workload)
     return line
 
 
@@ -530,7 +543,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch16"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.WORKLOADS) + ["batch16"],
+                    help="the default is the headline workload; the others are for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forward-only", action="store_true")
     args = ap.parse_args()

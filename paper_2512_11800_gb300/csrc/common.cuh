@@ -362,10 +362,16 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
         const bool left = (j <= 2);
         const float zb = left ? R.z[0] : R.z[3];
         const float far = left ? zb - R.span : zb + R.span;
-        const float ff = kernel_poly(R, e, far);
-        const float fz = kernel_poly(R, e, zb);
-        const bool outer = (ff > 0.0f) != (fz > 0.0f);
         const bool inner = j == 2;
+        // The nodes of the representation through y interlace with the Gauss
+        // nodes, and K(., y) > 0 on the root-free interval around y.  Between
+        // `far` and y lie: the outer root (if any) and, for j == 2, exactly one
+        // interior root.  So the outer root exists iff K(far) < 0 (j = 1, 3) or
+        // K(far) > 0 (j = 2).  Testing the sign at the outer Gauss node instead
+        // fails when a root sits within rounding of that node (y next to the
+        // neighbouring node).
+        const float ff = kernel_poly(R, e, far);
+        const bool outer = (ff < 0.0f) != inner;
         const int ns = (int)outer + (int)inner;
         float acc = 0.0f;
         // At most two root solves, through one copy of the solver so that

@@ -141,8 +141,11 @@ __global__ void k_reconstruct(Params p, const void* __restrict__ moments, int64_
 }
 
 // ---------------------------------------------------------------- quadrature pass
+#ifndef MB_SHADE_MIN_CTAS
+#define MB_SHADE_MIN_CTAS 3      // resident CTAs per SM the register budget is sized for
+#endif
 template <int NI, bool SAVE>
-__global__ void __launch_bounds__(TPB, 3) k_shade(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
+__global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                                                const int32_t* __restrict__ ids, const int2* __restrict__ ranges,
                                                int64_t P, int64_t npix, const StatusWords* sw,
                                                const float* __restrict__ recon, const void* __restrict__ moments,
