@@ -48,13 +48,19 @@ FP32_LANES_PER_SM = 128
 # workload divided by its pixel pairs).  The ALU roofline of a kernel is
 # this work over its time against the FP32 peak.
 FP32_FLOPS_PER_PAIR = {
-    "k_shade": 1524.0,
+    "k_shade": 1473.0,
     "k_bwd_quadrature": 1663.0,      # with saved bound queries
+}
+# DRAM bytes (read + write) per pair of the same captures: the saved bound
+# queries (64 B a pair) dominate; scaled to a launch by its pixel pairs.
+DRAM_BYTES_PER_PAIR = {
+    "k_shade": 71.1,
+    "k_bwd_quadrature": 69.8,
 }
 # Thread instructions per pair from the same captures (issue-rate view:
 # peak = SMs x 4 schedulers x 32 lanes x clock).
 THREAD_INST_PER_PAIR = {
-    "k_shade": 1969.0,
+    "k_shade": 1934.0,
     "k_bwd_quadrature": 1982.0,
 }
 
@@ -198,10 +204,12 @@ def roofline(kernel, ms, pairs, sm_max):
     issue_peak = SM_COUNT * 4 * 32 * sm_max * 1e6                          # thread instructions / s
     issue = THREAD_INST_PER_PAIR[kernel] * pairs / (ms * 1e-3)
     return dict(kernel=kernel, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=None, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel], issue_frac=issue / issue_peak,
+                traffic=DRAM_BYTES_PER_PAIR[kernel] * pairs, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel],
+                issue_frac=issue / issue_peak,
                 peak_note="FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock); executed FP32 flops per pixel "
                           "pair from ncu opcode counts; issue_frac = thread instructions per pair x pairs / time over "
-                          "%d SMs x 4 schedulers x 32 lanes x clock" % (SM_COUNT, FP32_LANES_PER_SM, sm_max, SM_COUNT))
+                          "%d SMs x 4 schedulers x 32 lanes x clock; traffic = ncu DRAM bytes per pair on the "
+                          "200k/720p workload x pairs" % (SM_COUNT, FP32_LANES_PER_SM, sm_max, SM_COUNT))
 
 
 class Frame:
