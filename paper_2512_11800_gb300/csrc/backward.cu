@@ -17,12 +17,14 @@ __device__ __forceinline__ float load_m0(const Params& p, const void* moments, i
 
 constexpr int GSTRIDE = 28;   // floats per record gradient (NGRAD padded)
 
-// Adds one staged batch's per-record sums (fields 0..nf-1) to the record gradients.
-__device__ __forceinline__ void flush_batch(const float* s_acc, int nb, int nf, const int32_t* __restrict__ ids,
-                                            int first, int64_t rec_base, float* __restrict__ grec) {
+// Adds one staged batch's per-record gradients (fields 0..nf-1, expanded from
+// the compact sums s_acc[k][nk]) to the record gradients.
+__device__ __forceinline__ void flush_batch(const float* s_rec, const float* s_acc, int nb, int nk, int nf,
+                                            const int32_t* __restrict__ ids, int first, int64_t rec_base,
+                                            float* __restrict__ grec) {
     for (int q = threadIdx.x; q < nb * nf; q += TPB) {
         const int k = q / nf, f = q - k * nf;
-        const float v = s_acc[k * NGRAD + f];
+        const float v = expand_geometry(s_rec + k * REC, s_acc + k * nk, f);
         if (v != 0.0f) atomicAdd(&grec[(rec_base + ids[first + k]) * GSTRIDE + f], v);
     }
 }
@@ -43,7 +45,7 @@ __global__ void __launch_bounds__(TPB, 2)
     extern __shared__ float4 s_raw[];
     __shared__ int s_slot;
     float* s_rec = reinterpret_cast<float*>(s_raw);
-    float* s_acc = s_rec + REC * p.batch;             // [batch][NGRAD]
+    float* s_acc = s_rec + REC * p.batch;             // [batch][NK_QUAD] compact sums
     // saved queries exist only when the frame's pixel pairs fit the capacity
     // (the status word then carries MB3DGS_ERR_CAPACITY)
     const bool any = sw->n_valid != 0 && !(SAVED && sw->n_pixpairs > (unsigned long long)qcap);
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(TPB, 2)
         const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         for (int b = 0; b * p.batch < n; ++b) {
-            for (int q = threadIdx.x; q < p.batch * NGRAD; q += TPB) s_acc[q] = 0.0f;
+            for (int q = threadIdx.x; q < p.batch * NK_QUAD; q += TPB) s_acc[q] = 0.0f;
             const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
             for (int k = 0; k < nb; ++k) {
                 const float* r = s_rec + k * REC;
@@ -84,16 +86,16 @@ __global__ void __launch_bounds__(TPB, 2)
                     const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
                     const PairOut po = pair_backward<NI, SAVED>(p, R, g, a, pa.gP, B, qp);
                     if (SAVED) qp += nq;
-                    geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, po.g_mu, po.g_Sig, po.g_what, acc);
-                    acc[G_RGB + 0] = pa.gS[0] * po.O;
-                    acc[G_RGB + 1] = pa.gS[1] * po.O;
-                    acc[G_RGB + 2] = pa.gS[2] * po.O;
+                    geometry_adjoint_compact(r, dx, dy, c.rlen, g, po.g_mu, po.g_Sig, po.g_what, acc);
+                    acc[K_RGB + 0] = pa.gS[0] * po.O;
+                    acc[K_RGB + 1] = pa.gS[1] * po.O;
+                    acc[K_RGB + 2] = pa.gS[2] * po.O;
                 }
                 const float v = reduce_scatter32(acc);
-                if (lane < NGRAD && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+                if (lane < NK_QUAD && v != 0.0f) atomicAdd(&s_acc[k * NK_QUAD + lane], v);
             }
             __syncthreads();
-            flush_batch(s_acc, nb, NGRAD, ids, c.start + b * p.batch, c.rec_base, grec);
+            flush_batch(s_rec, s_acc, nb, NK_QUAD, NGRAD, ids, c.start + b * p.batch, c.rec_base, grec);
             __syncthreads();
         }
         if (c.inside) {
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(TPB, 3)
     extern __shared__ float4 s_raw[];
     __shared__ int s_slot;
     float* s_rec = reinterpret_cast<float*>(s_raw);
-    float* s_acc = s_rec + REC * p.batch;             // [batch][NGRAD]
+    float* s_acc = s_rec + REC * p.batch;             // [batch][NK_MOM] compact sums
     const bool any = sw->n_valid != 0;
     const int lane = threadIdx.x & 31;
     for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
@@ -133,35 +135,46 @@ __global__ void __launch_bounds__(TPB, 3)
         const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         for (int b = 0; b * p.batch < n; ++b) {
-            for (int q = threadIdx.x; q < p.batch * NGRAD; q += TPB) s_acc[q] = 0.0f;
+            for (int q = threadIdx.x; q < p.batch * NK_MOM; q += TPB) s_acc[q] = 0.0f;
             const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
             for (int k = 0; k < nb; ++k) {
                 const float* r = s_rec + k * REC;
                 const bool active = c.inside && rect_contains(r, c.px, c.py);
                 if (!__any_sync(0xffffffffu, active)) continue;
-                float acc[32];
+                float acc[NK_MOM];
 #pragma unroll
-                for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
+                for (int f = 0; f < NK_MOM; ++f) acc[f] = 0.0f;
                 if (active) {
                     const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
                     const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
                     float g_mu = 0.0f, g_Sig = 0.0f, g_what = 0.0f;
                     moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
-                    geometry_adjoint(r, dx, dy, c.rlen, c.r2, g, g_mu, g_Sig, g_what, acc);
+                    geometry_adjoint_compact(r, dx, dy, c.rlen, g, g_mu, g_Sig, g_what, acc);
                 }
-                const float v = reduce_scatter32(acc);
-                if (lane < G_RGB && v != 0.0f) atomicAdd(&s_acc[k * NGRAD + lane], v);
+                const float v = reduce_scatter16(acc);
+                if (lane < NK_MOM && v != 0.0f) atomicAdd(&s_acc[k * NK_MOM + lane], v);
             }
             __syncthreads();
-            flush_batch(s_acc, nb, G_RGB, ids, c.start + b * p.batch, c.rec_base, grec);
+            flush_batch(s_rec, s_acc, nb, NK_MOM, G_RGB, ids, c.start + b * p.batch, c.rec_base, grec);
             __syncthreads();
         }
     }
 }
 
 // ---------------------------------------------------------------- preprocessing adjoint
-MB_HD void sh_grad_basis(const Params& p, double x, double y, double z, double Y[16], double dY[16][3]) {
-    const double xx = x * x, yy = y * y, zz = z * z;
+// float or double 3-vector helpers of the preprocessing adjoint
+template <typename T>
+MB_HD void cross3t(const T a[3], const T b[3], T c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+template <typename T>
+MB_HD T dot3t(const T a[3], const T b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+template <typename T>
+MB_HD void sh_grad_basis(const Params& p, T x, T y, T z, T Y[16], T dY[16][3]) {
+    const T xx = x * x, yy = y * y, zz = z * z;
     const float* c = p.sh_c;
     Y[0] = c[0]; dY[0][0] = dY[0][1] = dY[0][2] = 0.0;
     Y[1] = -c[1] * y; dY[1][0] = 0; dY[1][1] = -c[1]; dY[1][2] = 0;
@@ -184,6 +197,7 @@ MB_HD void sh_grad_basis(const Params& p, double x, double y, double z, double Y
     Y[15] = -c[15] * x * (xx - 3 * yy); dY[15][0] = -c[15] * (3 * xx - 3 * yy); dY[15][1] = 6 * c[15] * x * y; dY[15][2] = 0;
 }
 
+template <typename T>
 MB_HD void preprocess_bwd_one(const Params& p, const ViewTable& vt, const float* __restrict__ means,
                               const float* __restrict__ scales, const float* __restrict__ quats,
                               const float* __restrict__ weights, const float* __restrict__ sh, int64_t P, int sh_deg,
@@ -191,19 +205,19 @@ MB_HD void preprocess_bwd_one(const Params& p, const ViewTable& vt, const float*
                               float* __restrict__ d_means, float* __restrict__ d_scales, float* __restrict__ d_quats,
                               float* __restrict__ d_weights, float* __restrict__ d_sh) {
     const int K = (sh_deg + 1) * (sh_deg + 1);
-    double gmu[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gw = 0;
-    double gsh[48];
+    T gmu[3] = {0, 0, 0}, gs[3] = {0, 0, 0}, gq[4] = {0, 0, 0, 0}, gw = 0;
+    T gsh[48];
     for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.0;
-    double mu[3], s[3], q[4];
+    T mu[3], s[3], q[4];
     for (int k = 0; k < 3; ++k) { mu[k] = means[3 * i + k]; s[k] = scales[3 * i + k]; }
     for (int k = 0; k < 4; ++k) q[k] = quats[4 * i + k];
-    const double w = weights[i];
-    const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const double qw = q[0] / qn, qx = q[1] / qn, qy = q[2] / qn, qz = q[3] / qn;
-    const double Rq[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+    const T w = weights[i];
+    const T qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const T qw = q[0] / qn, qx = q[1] / qn, qy = q[2] / qn, qz = q[3] / qn;
+    const T Rq[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
                              {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
                              {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-    double gRq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    T gRq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int v = 0; v < vt.n_views; ++v) {
         const int64_t idx = (int64_t)v * P + i;
         const float* r = rec + idx * REC;
@@ -211,78 +225,76 @@ MB_HD void preprocess_bwd_one(const Params& p, const ViewTable& vt, const float*
         if (!(flags & 1)) continue;
         const float* G = grec + idx * GSTRIDE;
         const ViewDesc& V = vt.v[v];
-        double Rv[3][3], muc[3], Rg[3][3];
+        T Rv[3][3], muc[3], Rg[3][3];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) Rv[a][b] = V.R[3 * a + b];
         for (int a = 0; a < 3; ++a) {
-            muc[a] = Rv[a][0] * mu[0] + Rv[a][1] * mu[1] + Rv[a][2] * mu[2] + (double)V.t[a];
+            muc[a] = Rv[a][0] * mu[0] + Rv[a][1] * mu[1] + Rv[a][2] * mu[2] + (T)V.t[a];
             for (int b = 0; b < 3; ++b) Rg[a][b] = Rv[a][0] * Rq[0][b] + Rv[a][1] * Rq[1][b] + Rv[a][2] * Rq[2][b];
         }
-        double M[3][3];
+        T M[3][3];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) M[a][b] = Rg[b][a] / s[a];
-        const double fx = V.fx, fy = V.fy, cx = V.cx, cy = V.cy;
-        const double da[3] = {((double)r[R_AX] - cx) / fx, ((double)r[R_AY] - cy) / fy, 1.0};
-        double ga[3], mx[3], my[3], og[3];
+        const T fx = V.fx, fy = V.fy, cx = V.cx, cy = V.cy;
+        const T da[3] = {((T)r[R_AX] - cx) / fx, ((T)r[R_AY] - cy) / fy, 1.0};
+        T ga[3], mx[3], my[3], og[3];
         for (int a = 0; a < 3; ++a) {
             ga[a] = M[a][0] * da[0] + M[a][1] * da[1] + M[a][2];
             mx[a] = M[a][0] / fx;
             my[a] = M[a][1] / fy;
             og[a] = -(M[a][0] * muc[0] + M[a][1] * muc[1] + M[a][2] * muc[2]);
         }
-        double Gc0[3], Gcx[3], Gcy[3];
+        T Gc0[3], Gcx[3], Gcy[3];
         for (int k = 0; k < 3; ++k) { Gc0[k] = G[G_C0 + k]; Gcx[k] = G[G_CX + k]; Gcy[k] = G[G_CY + k]; }
-        const double Go0 = G[G_O], Gox = G[G_O + 1], Goy = G[G_O + 2];
+        const T Go0 = G[G_O], Gox = G[G_O + 1], Goy = G[G_O + 2];
         // c = a x b: dL/da = b x G, dL/db = G x a
-        double Gog[3], Gga[3], Gmx[3], Gmy[3], t1[3], t2[3], t3[3];
-        cross3(ga, Gc0, t1); cross3(mx, Gcx, t2); cross3(my, Gcy, t3);
+        T Gog[3], Gga[3], Gmx[3], Gmy[3], t1[3], t2[3], t3[3];
+        cross3t(ga, Gc0, t1); cross3t(mx, Gcx, t2); cross3t(my, Gcy, t3);
         for (int k = 0; k < 3; ++k) Gog[k] = t1[k] + t2[k] + t3[k] + Go0 * ga[k] + Gox * mx[k] + Goy * my[k];
-        cross3(Gc0, og, t1);
-        for (int k = 0; k < 3; ++k) Gga[k] = t1[k] + (double)G[G_GA + k] + Go0 * og[k];
-        cross3(Gcx, og, t1);
-        for (int k = 0; k < 3; ++k) Gmx[k] = t1[k] + (double)G[G_MX + k] + Gox * og[k];
-        cross3(Gcy, og, t1);
-        for (int k = 0; k < 3; ++k) Gmy[k] = t1[k] + (double)G[G_MY + k] + Goy * og[k];
-        double GM[3][3];
+        cross3t(Gc0, og, t1);
+        for (int k = 0; k < 3; ++k) Gga[k] = t1[k] + (T)G[G_GA + k] + Go0 * og[k];
+        cross3t(Gcx, og, t1);
+        for (int k = 0; k < 3; ++k) Gmx[k] = t1[k] + (T)G[G_MX + k] + Gox * og[k];
+        cross3t(Gcy, og, t1);
+        for (int k = 0; k < 3; ++k) Gmy[k] = t1[k] + (T)G[G_MY + k] + Goy * og[k];
+        T GM[3][3];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
                 GM[a][b] = -Gog[a] * muc[b] + Gga[a] * da[b] + (b == 0 ? Gmx[a] / fx : 0.0) + (b == 1 ? Gmy[a] / fy : 0.0);
-        double Gmuc[3];
+        T Gmuc[3];
         for (int b = 0; b < 3; ++b) Gmuc[b] = -(M[0][b] * Gog[0] + M[1][b] * Gog[1] + M[2][b] * Gog[2]);
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) gs[a] -= GM[a][b] * Rg[b][a] / (s[a] * s[a]);
-        double GRg[3][3];
+        T GRg[3][3];
         for (int b = 0; b < 3; ++b)
             for (int a = 0; a < 3; ++a) GRg[b][a] = GM[a][b] / s[a];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) gRq[a][b] += Rv[0][a] * GRg[0][b] + Rv[1][a] * GRg[1][b] + Rv[2][a] * GRg[2][b];
         for (int b = 0; b < 3; ++b) gmu[b] += Rv[0][b] * Gmuc[0] + Rv[1][b] * Gmuc[1] + Rv[2][b] * Gmuc[2];
-        gw += (double)G[G_LNW] / w;
+        gw += (T)G[G_LNW] / w;
         // SH colour at normalize(mu - eye)
-        double eye[3];
+        T eye[3];
         for (int a = 0; a < 3; ++a) eye[a] = -(Rv[0][a] * V.t[0] + Rv[1][a] * V.t[1] + Rv[2][a] * V.t[2]);
-        double dv[3] = {mu[0] - eye[0], mu[1] - eye[1], mu[2] - eye[2]};
-        const double dn = sqrt(dot3(dv, dv));
-        const double d[3] = {dv[0] / dn, dv[1] / dn, dv[2] / dn};
-        double Y[16], dY[16][3];
-        sh_grad_basis(p, d[0], d[1], d[2], Y, dY);
-        double gd[3] = {0, 0, 0};
+        T dv[3] = {mu[0] - eye[0], mu[1] - eye[1], mu[2] - eye[2]};
+        const T dn = sqrt(dot3t(dv, dv));
+        const T d[3] = {dv[0] / dn, dv[1] / dn, dv[2] / dn};
+        T Y[16], dY[16][3];
+        sh_grad_basis<T>(p, d[0], d[1], d[2], Y, dY);
+        T gd[3] = {0, 0, 0};
         for (int ch = 0; ch < 3; ++ch) {
-            double raw = 0.5;
-            for (int k = 0; k < K; ++k) raw += Y[k] * sh[(i * K + k) * 3 + ch];
-            if (!(raw > 0.0)) continue;
-            const double gc = G[G_RGB + ch];
+            if (!(r[R_RGB + ch] > 0.0f)) continue;   // colour clamped at 0 in the forward record
+            const T gc = G[G_RGB + ch];
             for (int k = 0; k < K; ++k) {
                 gsh[k * 3 + ch] += gc * Y[k];
-                const double f = sh[(i * K + k) * 3 + ch];
+                const T f = sh[(i * K + k) * 3 + ch];
                 for (int a = 0; a < 3; ++a) gd[a] += gc * f * dY[k][a];
             }
         }
-        const double dg = dot3(d, gd);
+        const T dg = dot3t(d, gd);
         for (int a = 0; a < 3; ++a) gmu[a] += (gd[a] - d[a] * dg) / dn;
     }
     // R(q-hat) and the normalisation q-hat = q / |q|
-    double gqh[4];
+    T gqh[4];
     gqh[0] = 2 * (-qz * gRq[0][1] + qy * gRq[0][2] + qz * gRq[1][0] - qx * gRq[1][2] - qy * gRq[2][0] + qx * gRq[2][1]);
     gqh[1] = 2 * (qy * gRq[0][1] + qz * gRq[0][2] + qy * gRq[1][0] - 2 * qx * gRq[1][1] - qw * gRq[1][2] +
                   qz * gRq[2][0] + qw * gRq[2][1] - 2 * qx * gRq[2][2]);
@@ -290,8 +302,8 @@ MB_HD void preprocess_bwd_one(const Params& p, const ViewTable& vt, const float*
                   qw * gRq[2][0] + qz * gRq[2][1] - 2 * qy * gRq[2][2]);
     gqh[3] = 2 * (-2 * qz * gRq[0][0] - qw * gRq[0][1] + qx * gRq[0][2] + qw * gRq[1][0] - 2 * qz * gRq[1][1] +
                   qy * gRq[1][2] + qx * gRq[2][0] + qy * gRq[2][1]);
-    const double qh[4] = {qw, qx, qy, qz};
-    const double pr = qh[0] * gqh[0] + qh[1] * gqh[1] + qh[2] * gqh[2] + qh[3] * gqh[3];
+    const T qh[4] = {qw, qx, qy, qz};
+    const T pr = qh[0] * gqh[0] + qh[1] * gqh[1] + qh[2] * gqh[2] + qh[3] * gqh[3];
     for (int k = 0; k < 4; ++k) gq[k] = (gqh[k] - qh[k] * pr) / qn;
     for (int k = 0; k < 3; ++k) {
         d_means[3 * i + k] = (float)gmu[k];
@@ -310,8 +322,10 @@ __global__ void k_preprocess_bwd(Params p, ViewTable vt, const float* __restrict
                                  float* __restrict__ d_quats, float* __restrict__ d_weights, float* __restrict__ d_sh) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P) return;
-    preprocess_bwd_one(p, vt, means, scales, quats, weights, sh, P, sh_deg, rec, grec, i, d_means, d_scales, d_quats,
-                       d_weights, d_sh);
+    // FP32: the chain rule needs no more (gradients to ~1e-6 relative); the
+    // forward keeps FP64 for the cancelling record coefficients
+    preprocess_bwd_one<float>(p, vt, means, scales, quats, weights, sh, P, sh_deg, rec, grec, i, d_means, d_scales,
+                              d_quats, d_weights, d_sh);
 }
 
 // Pass 1 (zeroes the record gradients first).

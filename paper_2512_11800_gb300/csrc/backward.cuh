@@ -415,6 +415,58 @@ MB_HD void geometry_adjoint(const float* __restrict__ r, float dx, float dy, flo
     out[G_LNW] += g.what * g_what;
 }
 
+// Compact form of the geometry adjoint.  With g = g_a + dx m_x + dy m_y and
+// v = c0 + dx cx + dy cy, the 22 record-coefficient derivatives of a pair are
+// 2 g_k g_dd {1, dx, dy}, 2 v_k g_c2 {1, dx, dy}, g_od {1, dx, dy} and
+// w-hat g_what; summed over a record's pixels they only need the 16 pixel
+// moments g_dd {1, dx, dy, dx^2, dx dy, dy^2}, g_c2 {same}, g_od {1, dx, dy}
+// and w-hat g_what, expanded once per record with its vectors
+// (expand_geometry).  Pass 1 adds the 3 colour fields.
+enum CompactField { K_DD = 0, K_C2 = 6, K_OD = 12, K_LNW = 15, K_RGB = 16, NK_MOM = 16, NK_QUAD = 19 };
+
+MB_HD void geometry_adjoint_compact(const float* __restrict__ r, float dx, float dy, float rlen, const Gauss1D& g,
+                                    float g_mu, float g_Sig, float g_what, float out[]) {
+    const float vx = fmaf(dy, r[R_CY + 0], fmaf(dx, r[R_CX + 0], r[R_C0 + 0]));
+    const float vy = fmaf(dy, r[R_CY + 1], fmaf(dx, r[R_CX + 1], r[R_C0 + 1]));
+    const float vz = fmaf(dy, r[R_CY + 2], fmaf(dx, r[R_CX + 2], r[R_C0 + 2]));
+    const float cross2 = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    const float gx = fmaf(dy, r[R_MY + 0], fmaf(dx, r[R_MX + 0], r[R_GA + 0]));
+    const float gy = fmaf(dy, r[R_MY + 1], fmaf(dx, r[R_MX + 1], r[R_GA + 1]));
+    const float gz = fmaf(dy, r[R_MY + 2], fmaf(dx, r[R_MX + 2], r[R_GA + 2]));
+    const float dd = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    const float inv = 1.0f / dd;
+    const float g_dd = inv * (-0.5f * g.Sig * g_Sig - g.mu * g_mu + 0.5f * g.what * cross2 * inv * g_what);
+    const float g_od = -rlen * inv * g_mu;
+    const float g_c2 = -0.5f * g.what * inv * g_what;
+    const float m[6] = {1.0f, dx, dy, dx * dx, dx * dy, dy * dy};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        out[K_DD + i] = fmaf(g_dd, m[i], out[K_DD + i]);
+        out[K_C2 + i] = fmaf(g_c2, m[i], out[K_C2 + i]);
+    }
+    out[K_OD + 0] += g_od;
+    out[K_OD + 1] = fmaf(g_od, dx, out[K_OD + 1]);
+    out[K_OD + 2] = fmaf(g_od, dy, out[K_OD + 2]);
+    out[K_LNW] = fmaf(g.what, g_what, out[K_LNW]);
+}
+
+// Record-coefficient derivative f (GradField) from the compact sums s of one record.
+MB_HD float expand_geometry(const float* __restrict__ r, const float* __restrict__ s, int f) {
+    if (f >= G_RGB) return s[K_RGB + f - G_RGB];
+    if (f >= G_LNW) return s[K_LNW];
+    if (f >= G_O) return s[K_OD + f - G_O];
+    // f in [G_C0, G_O): block b (0: c0/g_a, 1: cx/m_x, 2: cy/m_y), component k
+    const bool geo = f >= G_GA;
+    const int b = ((f - (geo ? G_GA : G_C0)) / 3), k = (f - (geo ? G_GA : G_C0)) % 3;
+    const float* S = s + (geo ? K_DD : K_C2);
+    const float a0 = r[(geo ? R_GA : R_C0) + k], a1 = r[(geo ? R_MX : R_CX) + k], a2 = r[(geo ? R_MY : R_CY) + k];
+    // moments for {1, dx, dy} x {1, dx, dy}: row b of [[S0,S1,S2],[S1,S3,S4],[S2,S4,S5]]
+    const float s0 = b == 0 ? S[0] : (b == 1 ? S[1] : S[2]);
+    const float s1 = b == 0 ? S[1] : (b == 1 ? S[3] : S[4]);
+    const float s2 = b == 0 ? S[2] : (b == 1 ? S[4] : S[5]);
+    return 2.0f * fmaf(a0, s0, fmaf(a1, s1, a2 * s2));
+}
+
 #ifdef __CUDACC__
 // Warp reduce-scatter of 32 per-lane values: lane f returns the warp sum of
 // v[f] (31 shuffles instead of 32 x 5 for per-field butterflies).  All 32
@@ -432,6 +484,23 @@ __device__ __forceinline__ float reduce_scatter32(float v[32]) {
         }
     }
     return v[0];
+}
+
+// Warp reduction of 16 per-lane values: lanes f and f + 16 return the warp
+// sum of v[f] (16 shuffles).  All 32 lanes must call it.
+__device__ __forceinline__ float reduce_scatter16(float v[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 #endif
 

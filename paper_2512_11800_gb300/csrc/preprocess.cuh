@@ -15,15 +15,15 @@ MB_HD double dot3(const double a[3], const double b[3]) {
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
-MB_HD float sh_color_channel(const Params& p, const float* __restrict__ sh, int K, int c, double x, double y,
-                                  double z) {
+// SH colour in FP32 (no cancellation to guard against; FP64 is slow on GB300).
+MB_HD float sh_color_channel(const Params& p, const float* __restrict__ sh, int K, int c, float x, float y, float z) {
     const float* f = sh + c;  // stride 3
-    double acc = p.sh_c[0] * f[0];
+    float acc = p.sh_c[0] * f[0];
     if (K > 1) {
         acc += p.sh_c[1] * (-y) * f[3 * 1] + p.sh_c[2] * z * f[3 * 2] + p.sh_c[3] * (-x) * f[3 * 3];
     }
     if (K > 4) {
-        const double xx = x * x, yy = y * y, zz = z * z;
+        const float xx = x * x, yy = y * y, zz = z * z;
         acc += p.sh_c[4] * (x * y) * f[3 * 4] + p.sh_c[5] * (-y * z) * f[3 * 5] +
                p.sh_c[6] * (2 * zz - xx - yy) * f[3 * 6] + p.sh_c[7] * (-x * z) * f[3 * 7] +
                p.sh_c[8] * (xx - yy) * f[3 * 8];
@@ -35,8 +35,8 @@ MB_HD float sh_color_channel(const Params& p, const float* __restrict__ sh, int 
                    p.sh_c[15] * (-x * (xx - 3 * yy)) * f[3 * 15];
         }
     }
-    acc += 0.5;
-    return (float)(acc > 0.0 ? acc : 0.0);
+    acc += 0.5f;
+    return acc > 0.0f ? acc : 0.0f;
 }
 
 MB_HD void preprocess_one(const Params& p, const ViewDesc& V, const float* __restrict__ means,
@@ -205,7 +205,7 @@ MB_HD void preprocess_one(const Params& p, const ViewDesc& V, const float* __res
     const double dn = sqrt(dx * dx + dy * dy + dz * dz);
     dx /= dn; dy /= dn; dz /= dn;
     const int K = (sh_deg + 1) * (sh_deg + 1);
-    for (int c = 0; c < 3; ++c) r[R_RGB + c] = sh_color_channel(p, sh + i * 3 * K, K, c, dx, dy, dz);
+    for (int c = 0; c < 3; ++c) r[R_RGB + c] = sh_color_channel(p, sh + i * 3 * K, K, c, (float)dx, (float)dy, (float)dz);
     r[R_AX] = (float)ax;
     r[R_AY] = (float)ay;
     ri[R_RECT + 0] = x0; ri[R_RECT + 1] = y0; ri[R_RECT + 2] = x1; ri[R_RECT + 3] = y1;
