@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(TPB, 2)
     // (the status word then carries MB3DGS_ERR_CAPACITY)
     const bool any = sw->n_valid != 0 && !(SAVED && sw->n_pixpairs > (unsigned long long)qcap);
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
+    const float4* q_end = SAVED ? pq + (size_t)qcap * nq : nullptr;   // end of the saved queries
     const int lane = threadIdx.x & 31;
     for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
         PixelCtx c = pixel_ctx(vt, ranges, P, tile);
@@ -81,6 +82,10 @@ __global__ void __launch_bounds__(TPB, 2)
 #pragma unroll
                 for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
                 if (active) {
+                    // the pixel's saved queries are contiguous in pair order: start
+                    // fetching the next pair's into L2 while this one is processed
+                    if (SAVED && qp + 2 * nq <= q_end)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(qp + nq));
                     const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
                     const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
                     const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;

@@ -142,3 +142,62 @@ def test_query_capacity_overflow_is_reported(R):
     grads = R.backward(g, cam, tp, dr)
     torch.cuda.synchronize()
     assert all(torch.isfinite(v).all() for v in grads.values())
+
+
+def test_finite_differences_on_256_gaussians():
+    """Directional central differences of the FP64 oracle loss against the GPU
+    gradient for 256 Gaussians of the 1M/1080p scene: the loss is a random
+    linear function of the RGB of an 8x8 crop; the GPU differentiates the
+    full frame, the oracle only the Gaussians whose rectangles touch the
+    crop (the only ones that affect it).  Gaussians whose rectangle or
+    culling changes under the perturbation are skipped."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11800_gb300 import Rasterizer
+    R = Rasterizer()
+    sc, cam = scenes.workload("shells1M_1080p")
+    x0, y0, s = 956, 536, 8
+    rng = np.random.default_rng(7)
+    g_img = np.zeros((cam.height, cam.width, 3))
+    g_img[y0:y0 + s, x0:x0 + s] = rng.normal(size=(s, s, 3))
+    gg = gpu_grads(R, sc, cam, g_img, np.zeros((cam.height, cam.width)))
+    cfg = oracle_config()
+    rect = O.preprocess(sc, cam, cfg).rect.numpy()
+    touch = np.where((rect[:, 0] <= x0 + s - 1) & (rect[:, 2] >= x0) & (rect[:, 1] <= y0 + s - 1) &
+                     (rect[:, 3] >= y0))[0]
+    sub = sc.subset(touch)
+    for k in ["means", "scales", "quats", "weights", "sh"]:      # exact perturbations
+        setattr(sub, k, getattr(sub, k).astype(np.float64))
+    gcrop = g_img[y0:y0 + s, x0:x0 + s]
+    region = (x0, y0, s, s)
+    base, rect0 = O.render_loss(sub, cam, cfg, gcrop, region=region)
+    # GPU gradient of the chosen Gaussians, per parameter group
+    pick = rng.choice(len(touch), size=min(256, len(touch)), replace=False)
+    n_ok, errs = 0, []
+    for j in pick:
+        gi = touch[j]
+        v = {k: rng.normal(size=getattr(sc, k)[gi].shape) for k in ["means", "scales", "quats", "weights"]}
+        h = {"means": 1e-3 * float(sc.scales[gi].max()), "scales": 1e-4 * float(sc.scales[gi].max()),
+             "quats": 1e-4, "weights": 1e-4 * float(sc.weights[gi])}
+        dot = sum(float(np.dot(gg[k].reshape(getattr(sc, k).shape[0], -1)[gi], v[k].reshape(-1)) * h[k])
+                  for k in v)
+        vals = []
+        for sign in (1.0, -1.0):
+            pert = sub.subset(np.arange(len(touch)))
+            for k in v:
+                getattr(pert, k)[j] = getattr(sub, k)[j] + sign * h[k] * v[k]
+            loss, r = O.render_loss(pert, cam, cfg, gcrop, region=region)
+            if not np.array_equal(r.numpy(), rect0.numpy()):
+                break
+            vals.append(loss)
+        if len(vals) < 2:
+            continue
+        fd = (vals[0] - vals[1]) / 2.0
+        errs.append((fd, dot))
+        n_ok += 1
+    fd, an = np.array(errs).T
+    scale = np.abs(fd).max()
+    rel = np.abs(fd - an) / (np.abs(fd) + 1e-3 * scale + 1e-12)
+    print("FD on", n_ok, "Gaussians: median rel", float(np.median(rel)), "max", float(rel.max()))
+    assert n_ok >= 200
+    assert np.median(rel) < 1e-3 and np.quantile(rel, 0.95) < 2e-2
