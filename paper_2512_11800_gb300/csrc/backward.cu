@@ -116,7 +116,10 @@ __global__ void __launch_bounds__(TPB, 2)
 // ---------------------------------------------------------------- pass 2
 // Per pair: int psi d(d mu_i) through the reverse sweep of the moment
 // recurrence, chained to the record geometry (fields before G_RGB).
-__global__ void __launch_bounds__(TPB, 3)
+#ifndef MB_BWD_MOMENTS_MIN_CTAS
+#define MB_BWD_MOMENTS_MIN_CTAS 4
+#endif
+__global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
     k_bwd_moments(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec, const int32_t* __restrict__ ids,
                   const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWords* sw,
                   const float* __restrict__ recon, const float* __restrict__ psi_in, float* __restrict__ grec) {
@@ -339,11 +342,11 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
     float* grec = reinterpret_cast<float*>(ws + L.grec);
     if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (L.n_tiles == 0) return MB3DGS_OK;
-    const size_t smem = sizeof(float) * (REC + NGRAD) * p.batch;
+    const size_t smem = sizeof(float) * (REC + NK_QUAD) * p.batch;
     const bool saved_q = L.qcap > 0;
     auto k1 = p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true> : k_bwd_quadrature<3, false>)
                                  : (saved_q ? k_bwd_quadrature<0, true> : k_bwd_quadrature<0, false>);
-    if (!allow_dynamic_smem((const void*)k1, sizeof(float) * (REC + NGRAD) * TPB)) return MB3DGS_ERR_CUDA;
+    if (!allow_dynamic_smem((const void*)k1, sizeof(float) * (REC + NK_QUAD) * TPB)) return MB3DGS_ERR_CUDA;
     const TileLaunch t1 = tile_launch(p, L, ws, Q_BWD_QUAD, (const void*)k1, smem, st);
     count_launch();
     k1<<<t1.grid, TPB, smem, st>>>(
@@ -359,8 +362,8 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
 // Pass 2.
 int launch_backward_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
     if (L.n_tiles == 0) return MB3DGS_OK;
-    const size_t smem = sizeof(float) * (REC + NGRAD) * p.batch;
-    if (!allow_dynamic_smem((const void*)k_bwd_moments, sizeof(float) * (REC + NGRAD) * TPB)) return MB3DGS_ERR_CUDA;
+    const size_t smem = sizeof(float) * (REC + NK_MOM) * p.batch;
+    if (!allow_dynamic_smem((const void*)k_bwd_moments, sizeof(float) * (REC + NK_MOM) * TPB)) return MB3DGS_ERR_CUDA;
     const TileLaunch t2 = tile_launch(p, L, ws, Q_BWD_MOM, (const void*)k_bwd_moments, smem, st);
     count_launch();
     k_bwd_moments<<<t2.grid, TPB, smem, st>>>(
