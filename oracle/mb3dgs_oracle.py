@@ -527,7 +527,7 @@ def render(scene, cam, cfg: OracleConfig = None, region=None, params=None, probe
 
 
 # ----------------------------------------------------------------------------
-# tile binning (spec: bins by tile key only, no depth sort)
+# tile binning (by tile key only, no depth sort)
 # ----------------------------------------------------------------------------
 def bin_tiles(rect, width, height, tile_w=16, tile_h=16):
     """Tile lists of the pixel rectangles: for every tile (row-major) the
