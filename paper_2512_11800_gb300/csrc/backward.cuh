@@ -85,6 +85,18 @@ MB_HD void sym_update(float B[NB], float s, const float u[5], const float v[5]) 
     }
 }
 
+// B += s u u^T, i.e. Phi += s K_u^2
+MB_HD void sym_update_sq(float B[NB], float s, const float u[5]) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float su = s * u[k];
+        B[bidx(k, k)] = fmaf(su, u[k], B[bidx(k, k)]);
+        const float su2 = 2.0f * su;
+#pragma unroll
+        for (int l = k + 1; l < 5; ++l) B[bidx(k, l)] = fmaf(su2, u[l], B[bidx(k, l)]);
+    }
+}
+
 MB_HD float kdot(const Recon& R, const float Pa[5], const float Pb[5]) {
     return Pa[0] * Pb[0] + R.h[0] * Pa[1] * Pb[1] + R.h[1] * Pa[2] * Pb[2] + R.h[2] * Pa[3] * Pb[3] +
            R.h[3] * Pa[4] * Pb[4];
@@ -108,7 +120,7 @@ MB_HD void query_adjoint(const Params& p, const Recon& R, const QueryRec& q, flo
     float dF = c0 * dw0;
     float ey[5];
     kernel_coeffs(R, Py, ey);
-    sym_update(B, gq * c0 * w0 * w0, ey, ey);
+    sym_update_sq(B, gq * c0 * w0 * w0, ey);
     if (!left) B[0] += gq;      // the constant 1 of F = 1 - ...
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -190,15 +202,14 @@ struct Sample {
 };
 
 template <bool SAVED>
-MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float isq, int j,
-                       const float4* __restrict__ qin, Sample& s) {
+MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float isq, int j, float4 qv, Sample& s) {
     const float raw = fmaf(p.kappa * g.Sig, p.x_nodes[j], g.mu);
     s.t = fminf(fmaxf(raw, p.t_near), p.t_far);
     s.clamped = s.t != raw;
     float gj;
     warp_g(p, s.t, gj, s.dg);
     if (SAVED)
-        s.tau = unpack_query(qin[j], (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, s.q);
+        s.tau = unpack_query(qv, (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, s.q);
     else
         s.tau = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &s.q);
     s.b = (s.t - g.mu) * isq;
@@ -214,7 +225,8 @@ MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float 
 // instead of being solved again.  Streamed over the samples: interval j is
 // processed once samples j and j+1 are loaded, after which sample j's
 // adjoints are final and go through its bound query (one copy of the query
-// code, no per-sample arrays).
+// code, no per-sample arrays).  Saved queries are read one sample ahead of
+// their use, so each load overlaps a whole interval's arithmetic.
 template <int NI, bool SAVED = false>
 MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, float a, float gP, float B[NB],
                             const float4* __restrict__ qin = nullptr) {
@@ -229,11 +241,17 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
     const float tscale = g.what * g.Sig * 1.25331413731550025f;
     const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
     Sample c, n;
-    load_sample<SAVED>(p, R, g, isq, 0, qin, c);
+    float4 qa = make_float4(0.0f, 0.0f, 0.0f, 0.0f), qb = qa;
+    if (SAVED) {
+        qa = qin[0];
+        qb = qin[1];
+    }
+    load_sample<SAVED>(p, R, g, isq, 0, qa, c);
 #pragma unroll 1
     for (int j = 0; j <= N; ++j) {
         if (j < N) {
-            load_sample<SAVED>(p, R, g, isq, j + 1, qin, n);
+            load_sample<SAVED>(p, R, g, isq, j + 1, qb, n);
+            if (SAVED && j + 2 <= N) qb = qin[j + 2];
             // interval j: term = T_j ph(dtau) sig_j Delta_j and the penalty v^2
             const float Delta = n.t - c.t;
             const float dtr = n.tau - c.tau;
