@@ -178,7 +178,12 @@ static void make_params(const mb3dgs_config* c, Params& p) {
     p.two_over_a = (float)(2.0 / a);
     p.lam_is_m15 = c->warp_lambda == -1.5f;
     const int N = c->n_intervals;
-    for (int j = 0; j <= N; ++j) p.x_nodes[j] = (float)inv_normal_cdf((j + 0.5) / (N + 1));
+    for (int j = 0; j <= N; ++j) {
+        p.x_nodes[j] = (float)inv_normal_cdf((j + 0.5) / (N + 1));
+        const double b = (double)p.kappa * (double)p.x_nodes[j] / std::sqrt(2.0);
+        p.x_erf[j] = (float)std::erf(b);
+        p.x_gau[j] = (float)std::exp(-b * b);
+    }
     const double pi = M_PI;
     const double c0 = 0.5 / std::sqrt(pi), c1 = std::sqrt(3.0 / (4.0 * pi)), c2 = 0.5 * std::sqrt(15.0 / pi),
                  c20 = 0.25 * std::sqrt(5.0 / pi), c22 = 0.25 * std::sqrt(15.0 / pi),

@@ -195,7 +195,7 @@ struct PairOut {
 // instead of being solved again.
 // One sample t_j of a pair with its bound query and running adjoints.
 struct Sample {
-    float t, tau, dg, b, erf;   // sample, optical depth, warp slope, (t - mu)/(sqrt2 Sigma), erf(b)
+    float t, tau, dg, b, erf, gau;   // sample, optical depth, warp slope, b = (t - mu)/(sqrt2 Sigma), erf(b), e^{-b^2}
     bool clamped;               // t_j clamped to [t_n, t_f] (no derivative to mu, Sigma)
     QueryRec q;
     float gt, gtau;             // dL/dt_j, dL/dtau_j
@@ -213,7 +213,12 @@ MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float 
     else
         s.tau = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &s.q);
     s.b = (s.t - g.mu) * isq;
-    s.erf = erff(s.b);
+    s.erf = p.x_erf[j];
+    s.gau = p.x_gau[j];
+    if (s.clamped) {
+        s.erf = erff(s.b);
+        s.gau = expf(-s.b * s.b);
+    }
     s.gt = 0.0f;
     s.gtau = 0.0f;
 }
@@ -236,7 +241,6 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
     o.g_mu = 0.0f;
     o.g_Sig = 0.0f;
     o.g_what = 0.0f;
-    const float inv2s2 = 0.5f / g.Sig2;
     const float isq = 0.70710678118654752f / g.Sig;
     const float tscale = g.what * g.Sig * 1.25331413731550025f;
     const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
@@ -259,7 +263,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             const float dtau = pos ? dtr : 0.0f;
             const float Tj = expf(-c.tau);
             const float d0 = c.t - g.mu;
-            const float e0 = expf(-d0 * d0 * inv2s2);
+            const float e0 = c.gau;
             const float sig = g.what * e0;
             float ph, dph;
             if (dtau < 1e-4f) {
@@ -293,8 +297,8 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             if (gtij != 0.0f) {
                 o.g_what += gtij * tscale * (n.erf - c.erf) / fmaxf(g.what, 1e-30f);
                 o.g_Sig += gtij * tij / g.Sig;
-                const float c1 = gtij * dscale * expf(-n.b * n.b);
-                const float c0 = -gtij * dscale * expf(-c.b * c.b);
+                const float c1 = gtij * dscale * n.gau;
+                const float c0 = -gtij * dscale * c.gau;
                 n.gt += c1 * isq;
                 c.gt += c0 * isq;
                 o.g_mu -= (c1 + c0) * isq;

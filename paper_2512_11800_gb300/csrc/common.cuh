@@ -72,6 +72,10 @@ struct Params {
     float gl_y[5], gl_w[5];   // 5-point Gauss-Legendre rule for U[-1,1] (probability weights)
     int lam_is_m15;        // lambda == -1.5: powers via rsqrt
     float x_nodes[MAX_NODES];    // standard-normal sample nodes (App. B)
+    // A sample that is not clamped to [t_n, t_f] sits at mu + kappa Sigma x_j,
+    // so b_j = (t_j - mu) / (sqrt2 Sigma) = kappa x_j / sqrt2 is a constant of
+    // the node: erf(b_j) and e^{-b_j^2}, evaluated on the host in double.
+    float x_erf[MAX_NODES], x_gau[MAX_NODES];
     float sh_c[16];        // real SH normalisation constants
     float leg_to_pow[NMOM * NMOM]; // m-hat_k = sum_l leg_to_pow[k*9+l] I_l
     int strict;
@@ -604,14 +608,15 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
     // j-1 is accumulated once sample j is known
     const int N = NI > 0 ? NI : p.n_intervals;
     const float ks = p.kappa * g.Sig;
-    const float inv2s2 = 0.5f / g.Sig2;
     const float isq = 0.70710678118654752f / g.Sig;
     const float tscale = g.what * g.Sig * 1.25331413731550025f;
     float O = 0.0f, P = 0.0f;
     float t_prev = 0.0f, tau_prev = 0.0f, erf_prev = 0.0f;
+    float gau_prev = 0.0f;
 #pragma unroll 1
     for (int j = 0; j <= N; ++j) {
-        const float tj = fminf(fmaxf(fmaf(ks, p.x_nodes[j], g.mu), p.t_near), p.t_far);
+        const float raw = fmaf(ks, p.x_nodes[j], g.mu);
+        const float tj = fminf(fmaxf(raw, p.t_near), p.t_far);
         const float y = fmaf(2.0f, warp_only(p, tj), -1.0f);
         float tau;
         if (SAVE && qout) {
@@ -621,13 +626,17 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
         } else {
             tau = optical_depth(R, p.beta, y);
         }
-        const float erf_j = erff((tj - g.mu) * isq);
+        float erf_j = p.x_erf[j], gau_j = p.x_gau[j];
+        if (tj != raw) {
+            const float b = (tj - g.mu) * isq;
+            erf_j = erff(b);
+            gau_j = expf(-b * b);
+        }
         if (j > 0) {
             const float Delta = tj - t_prev;
             const float dtau = fmaxf(tau - tau_prev, 0.0f);
             const float Tj = expf(-tau_prev);
-            const float dt0 = t_prev - g.mu;
-            const float sig = g.what * expf(-dt0 * dt0 * inv2s2);
+            const float sig = g.what * gau_prev;
             const float ratio = dtau < 1e-6f ? fmaf(-0.5f, dtau, 1.0f) : -expm1f(-dtau) / dtau;
             O = fmaf(Tj * ratio, sig * Delta, O);
             const float tij = tscale * (erf_j - erf_prev);
@@ -637,6 +646,7 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
         t_prev = tj;
         tau_prev = tau;
         erf_prev = erf_j;
+        gau_prev = gau_j;
     }
     *pen += P;
     return O;
