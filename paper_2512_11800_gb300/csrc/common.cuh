@@ -291,38 +291,70 @@ MB_HD float christoffel_weight(const Recon& R, float x) {
     return isfinite(w) ? w : 0.0f;
 }
 
+// Monomial coefficients c of K(., y) = sum_k e_k pi_k (standardised x), from
+// Clenshaw's recurrence carried out on polynomials: r_4 = e_4,
+// r_k = e_k + (x - al_k) r_{k+1} - be_k r_{k+2} (be indexed as in pis), K = r_0.
+MB_HD void kernel_monomials(const Recon& R, const float e[5], float c[5]) {
+    const float r3_0 = fmaf(-R.al[3], e[4], e[3]);
+    const float r2_0 = fmaf(-R.al[2], r3_0, fmaf(-R.be[2], e[4], e[2]));
+    const float r2_1 = fmaf(-R.al[2], e[4], r3_0);
+    const float r1_0 = fmaf(-R.al[1], r2_0, fmaf(-R.be[1], r3_0, e[1]));
+    const float r1_1 = fmaf(-R.al[1], r2_1, fmaf(-R.be[1], e[4], r2_0));
+    const float r1_2 = fmaf(-R.al[1], e[4], r2_1);
+    c[0] = fmaf(-R.al[0], r1_0, fmaf(-R.be[0], r2_0, e[0]));
+    c[1] = fmaf(-R.al[0], r1_1, fmaf(-R.be[0], r2_1, r1_0));
+    c[2] = fmaf(-R.al[0], r1_2, fmaf(-R.be[0], e[4], r1_1));
+    c[3] = fmaf(-R.al[0], e[4], r1_2);
+    c[4] = e[4];
+}
+
+// One Laguerre step for a degree-4 polynomial with value f, f' and f''.
+MB_HD float laguerre_step(float x, float f, float fp, float fpp, float lo, float hi, bool right) {
+    const float q = sqrtf(fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 0.0f));
+    const float sq = f >= 0.0f ? q : -q;
+    const float den = right ? fp - sq : fp + sq;
+    const float step = den != 0.0f ? fdiv_(4.0f * f, den) : 0.0f;
+    float xn = x - step;
+    xn = fminf(fmaxf(xn, lo), hi);
+    return isfinite(xn) ? xn : x;
+}
+
 // Laguerre iteration towards the neighbouring root on one side.  For a
 // real-rooted polynomial the iterates move monotonically to the adjacent root
-// in the chosen direction, cubically near it.
-MB_HD float laguerre(const Recon& R, const float e[5], float x, float lo, float hi,
-                                          bool right) {
+// in the chosen direction, cubically near it.  All but the last step evaluate
+// the kernel polynomial by Horner's rule on its monomial coefficients c; the
+// last step evaluates it through the three-term recurrence (coefficients e),
+// which sets the accuracy of the root.
+MB_HD float laguerre(const Recon& R, const float e[5], const float c[5], float x, float lo, float hi,
+                     bool right) {
 #pragma unroll 1
-    for (int it = 0; it < LAG_ITERS; ++it) {
-        float p0 = 1.0f, p1 = x - R.al[0];
-        float d0 = 0.0f, d1 = 1.0f;
-        float s0 = 0.0f, s1 = 0.0f;
-        float f = e[0] + e[1] * p1, fp = e[1], fpp = 0.0f;
+    for (int it = 0; it < LAG_ITERS - 1; ++it) {
+        float f = c[4], d1 = 0.0f, d2 = 0.0f;
 #pragma unroll
-        for (int k = 1; k < 4; ++k) {
-            const float xa = x - R.al[k];
-            const float b = R.be[k - 1];
-            float p2 = fmaf(xa, p1, -b * p0);
-            float d2 = fmaf(xa, d1, fmaf(-b, d0, p1));
-            float s2 = fmaf(xa, s1, fmaf(-b, s0, 2.0f * d1));
-            f = fmaf(e[k + 1], p2, f);
-            fp = fmaf(e[k + 1], d2, fp);
-            fpp = fmaf(e[k + 1], s2, fpp);
-            p0 = p1; p1 = p2; d0 = d1; d1 = d2; s0 = s1; s1 = s2;
+        for (int k = 3; k >= 0; --k) {
+            d2 = fmaf(d2, x, d1);
+            d1 = fmaf(d1, x, f);
+            f = fmaf(f, x, c[k]);
         }
-        const float q = sqrtf(fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 0.0f));
-        const float sq = f >= 0.0f ? q : -q;
-        const float den = right ? fp - sq : fp + sq;
-        const float step = den != 0.0f ? fdiv_(4.0f * f, den) : 0.0f;
-        float xn = x - step;
-        xn = fminf(fmaxf(xn, lo), hi);
-        x = isfinite(xn) ? xn : x;
+        x = laguerre_step(x, f, d1, 2.0f * d2, lo, hi, right);
     }
-    return x;
+    float p0 = 1.0f, p1 = x - R.al[0];
+    float d0 = 0.0f, d1 = 1.0f;
+    float s0 = 0.0f, s1 = 0.0f;
+    float f = e[0] + e[1] * p1, fp = e[1], fpp = 0.0f;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const float xa = x - R.al[k];
+        const float b = R.be[k - 1];
+        float p2 = fmaf(xa, p1, -b * p0);
+        float d2 = fmaf(xa, d1, fmaf(-b, d0, p1));
+        float s2 = fmaf(xa, s1, fmaf(-b, s0, 2.0f * d1));
+        f = fmaf(e[k + 1], p2, f);
+        fp = fmaf(e[k + 1], d2, fp);
+        fpp = fmaf(e[k + 1], s2, fpp);
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2; s0 = s1; s1 = s2;
+    }
+    return laguerre_step(x, f, fp, fpp, lo, hi, right);
 }
 
 // Roots of one bound query, kept by the backward pass (standardised units).
@@ -377,6 +409,8 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
         const float ff = kernel_poly(R, e, far);
         const bool outer = (ff < 0.0f) != inner;
         const int ns = (int)outer + (int)inner;
+        float c[5];
+        kernel_monomials(R, e, c);
         float acc = 0.0f;
         // At most two root solves, through one copy of the solver so that
         // lanes needing one root of either kind iterate together: first the
@@ -389,7 +423,7 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
             const float x0 = in ? R.z[1] : far;
             const float lo = in ? R.z[0] : (left ? far : zb);
             const float hi = in ? R.z[1] : (left ? zb : far);
-            const float x = laguerre(R, e, x0, lo, hi, !in && left);
+            const float x = laguerre(R, e, c, x0, lo, hi, !in && left);
             acc += christoffel_weight(R, x);
             if (REC) {   // static indices keep the record in registers
                 if (sv == 0) rec->x[0] = x;
