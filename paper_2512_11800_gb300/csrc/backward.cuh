@@ -111,7 +111,7 @@ MB_HD void query_adjoint(const Params& p, const Recon& R, const QueryRec& q, flo
     float Py[5], Dy[5];
     pis_d(R, q.y, Py, Dy);
     const float Kyy = kdot(R, Py, Py);
-    const float w0 = 1.0f / Kyy;
+    const float w0 = fdiv_(1.0f, Kyy);   // Kyy >= 1
     const float K1yy = kdot(R, Dy, Py);
     const float dw0 = -2.0f * w0 * w0 * K1yy;
     const bool left = q.j <= 2;
@@ -133,7 +133,7 @@ MB_HD void query_adjoint(const Params& p, const Recon& R, const QueryRec& q, flo
         const float K1xx = kdot(R, Dx, Px);
         const float K1xy = kdot(R, Dx, Py);
         const float K1yx = kdot(R, Dy, Px);
-        const float rho = K1xy != 0.0f ? K1xx / K1xy : 0.0f;
+        const float rho = K1xy != 0.0f ? fdiv_(K1xx, K1xy) : 0.0f;
         dF = fmaf(sgn, 2.0f * w * w * rho * K1yx, dF);
         // Phi += s (K_x^2 - 2 rho K_x K_y) = s sym(e_x (e_x - 2 rho e_y)^T)
         float ex[5], v[5];
@@ -241,8 +241,11 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
     o.g_mu = 0.0f;
     o.g_Sig = 0.0f;
     o.g_what = 0.0f;
-    const float isq = 0.70710678118654752f / g.Sig;
-    const float tscale = g.what * g.Sig * 1.25331413731550025f;
+    const float iSig = 1.0f / g.Sig;
+    const float iSig2 = iSig * iSig;
+    const float isq = 0.70710678118654752f * iSig;
+    const float escale = g.Sig * 1.25331413731550025f;             // d tau_ij / d w-hat per erf difference
+    const float tscale = g.what * escale;
     const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
     Sample c, n;
     float4 qa = make_float4(0.0f, 0.0f, 0.0f, 0.0f), qb = qa;
@@ -265,14 +268,19 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             const float d0 = c.t - g.mu;
             const float e0 = c.gau;
             const float sig = g.what * e0;
+            // ph(x) = (1 - e^-x)/x and ph'(x) = (e^-x - ph(x))/x: Taylor series
+            // below x = 0.05 (truncation < 5e-10), where e^-x - ph cancels
             float ph, dph;
-            if (dtau < 1e-4f) {
-                ph = fmaf(dtau, fmaf(dtau, 1.0f / 6.0f, -0.5f), 1.0f);
-                dph = fmaf(dtau, 1.0f / 3.0f, -0.5f);
+            if (dtau < 0.05f) {
+                ph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, 1.0f / 120.0f, -1.0f / 24.0f), 1.0f / 6.0f), -0.5f),
+                          1.0f);
+                dph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, -1.0f / 144.0f, 1.0f / 30.0f), -0.125f), 1.0f / 3.0f),
+                           -0.5f);
             } else {
-                const float em = expf(-dtau);
-                ph = -expm1f(-dtau) / dtau;
-                dph = (em * (1.0f + dtau) - 1.0f) / (dtau * dtau);
+                const float xm = expm1f(-dtau);   // e^-x - 1
+                const float idt = fdiv_(1.0f, dtau);
+                ph = -xm * idt;
+                dph = (1.0f + xm - ph) * idt;
             }
             const float term = Tj * ph * sig * Delta;
             o.O += term;
@@ -288,21 +296,21 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             const float gD = a * Tj * ph * sig;
             n.gt += gD;
             c.gt -= gD;
-            const float sd = gsig * sig * d0 / g.Sig2;
+            const float sd = gsig * sig * d0 * iSig2;
             c.gt -= sd;
             o.g_mu += sd;
-            o.g_Sig += sd * d0 / g.Sig;
+            o.g_Sig += sd * d0 * iSig;
             o.g_what += gsig * e0;
             const float gtij = 2.0f * gP * v;
             if (gtij != 0.0f) {
-                o.g_what += gtij * tscale * (n.erf - c.erf) / fmaxf(g.what, 1e-30f);
-                o.g_Sig += gtij * tij / g.Sig;
+                o.g_what += gtij * escale * (n.erf - c.erf);
+                o.g_Sig += gtij * tij * iSig;
                 const float c1 = gtij * dscale * n.gau;
                 const float c0 = -gtij * dscale * c.gau;
                 n.gt += c1 * isq;
                 c.gt += c0 * isq;
                 o.g_mu -= (c1 + c0) * isq;
-                o.g_Sig -= (c1 * n.b + c0 * c.b) / g.Sig;
+                o.g_Sig -= (c1 * n.b + c0 * c.b) * iSig;
             }
         }
         // sample j is final: through its bound query to y_j and the moments
@@ -330,7 +338,7 @@ MB_HD void moment_adjoint(const Params& p, const Recon& R, const Gauss1D& g, con
     gm = fmaf(dgm, g.mu - cpt, gm);
     if (g.mu > p.t_near) {
         const float z = fmaf(p.two_over_a, cpt, 1.0f);
-        ddgm = p.G3 * (dgm / p.G2) / z;   // g'' = G3 z^(lambda-2)
+        ddgm = p.G3 * fdiv_(dgm, p.G2 * z);   // g'' = G3 z^(lambda-2)
     } else {
         ddgm = 0.0f;
     }
@@ -338,7 +346,8 @@ MB_HD void moment_adjoint(const Params& p, const Recon& R, const Gauss1D& g, con
     const float S = 2.0f * dgm * R.inv_s;
     const float dS = 2.0f * ddgm * R.inv_s;
     const float dn = p.t_near - g.mu;
-    const float bn = dn * (0.70710678118654752f / g.Sig);
+    const float iSg = 1.0f / g.Sig;
+    const float bn = dn * (0.70710678118654752f * iSg);
     const float en = expf(-bn * bn);
     const float un = fmaf(S, dn, A);
     const float w = g.what, Sg = g.Sig, S2 = g.Sig2;
@@ -381,15 +390,15 @@ MB_HD void moment_adjoint(const Params& p, const Recon& R, const Gauss1D& g, con
     {
         const float c = Mb[0];
         wb = fmaf(Sg * 1.25331413731550025f * erfcf(bn), c, wb);
-        Sgb = fmaf(M[0] / Sg, c, Sgb);
+        Sgb = fmaf(M[0] * iSg, c, Sgb);
         bnb = fmaf(-w * Sg * 1.41421356237309505f * en, c, bnb);
     }
     bnb = fmaf(-2.0f * bn * en, enb, bnb);
     Ab += unb;
     Sb = fmaf(dn, unb, Sb);
     mub = fmaf(-S, unb, mub);
-    mub = fmaf(-(0.70710678118654752f / Sg), bnb, mub);
-    Sgb = fmaf(-bn / Sg, bnb, Sgb);
+    mub = fmaf(-(0.70710678118654752f * iSg), bnb, mub);
+    Sgb = fmaf(-bn * iSg, bnb, Sgb);
     mub = fmaf(S, Ab, mub);
     mub = fmaf(dS, Sb, mub);
     *g_mu += mub;

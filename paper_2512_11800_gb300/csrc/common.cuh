@@ -153,7 +153,7 @@ MB_HD void warp_g(const Params& p, float t, float& g, float& dg) {
     if (p.lam_is_m15) {
         float r = rsqrt_(z);
         zl = r * r * r;          // z^-1.5
-        zl1 = zl / z;            // z^-2.5
+        zl1 = zl * (r * r);      // z^-2.5
     } else {
         zl = powf(z, p.warp_lambda);
         zl1 = zl / z;
@@ -671,7 +671,7 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
             const float dtau = fmaxf(tau - tau_prev, 0.0f);
             const float Tj = expf(-tau_prev);
             const float sig = g.what * gau_prev;
-            const float ratio = dtau < 1e-6f ? fmaf(-0.5f, dtau, 1.0f) : -expm1f(-dtau) / dtau;
+            const float ratio = dtau < 1e-6f ? fmaf(-0.5f, dtau, 1.0f) : fdiv_(-expm1f(-dtau), dtau);
             O = fmaf(Tj * ratio, sig * Delta, O);
             const float tij = tscale * (erf_j - erf_prev);
             const float v = fmaxf(tij - dtau, 0.0f);
