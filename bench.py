@@ -48,20 +48,20 @@ FP32_LANES_PER_SM = 128
 # workload divided by its pixel pairs).  The ALU roofline of a kernel is
 # this work over its time against the FP32 peak.
 FP32_FLOPS_PER_PAIR = {
-    "k_shade": 1473.0,
-    "k_bwd_quadrature": 1663.0,      # with saved bound queries
+    "k_shade": 1171.3,               # k_shade<3, save>: keeps the bound queries
+    "k_bwd_quadrature": 1247.5,      # k_bwd_quadrature<3, saved>
 }
 # DRAM bytes (read + write) per pair of the same captures: the saved bound
 # queries (64 B a pair) dominate; scaled to a launch by its pixel pairs.
 DRAM_BYTES_PER_PAIR = {
-    "k_shade": 71.1,
-    "k_bwd_quadrature": 69.8,
+    "k_shade": 71.5,
+    "k_bwd_quadrature": 70.6,
 }
 # Thread instructions per pair from the same captures (issue-rate view:
 # peak = SMs x 4 schedulers x 32 lanes x clock).
 THREAD_INST_PER_PAIR = {
-    "k_shade": 1934.0,
-    "k_bwd_quadrature": 1982.0,
+    "k_shade": 1776.3,
+    "k_bwd_quadrature": 1702.0,
 }
 
 
@@ -198,13 +198,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def roofline(kernel, ms, pairs, sm_max):
+def roofline(kernel, ms, pairs, sm_max, captured=True):
+    """captured=False: the launch is a variant without a capture of its own
+    (k_shade keeping no queries): flops and instructions are those of the
+    captured variant (it adds ~10 instructions a pair to store a query), and
+    traffic is null."""
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the max SM clock
     achieved = FP32_FLOPS_PER_PAIR[kernel] * pairs / (ms * 1e-3) / 1e12
     issue_peak = SM_COUNT * 4 * 32 * sm_max * 1e6                          # thread instructions / s
     issue = THREAD_INST_PER_PAIR[kernel] * pairs / (ms * 1e-3)
     return dict(kernel=kernel, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=DRAM_BYTES_PER_PAIR[kernel] * pairs, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel],
+                traffic=DRAM_BYTES_PER_PAIR[kernel] * pairs if captured else None, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel],
                 issue_frac=issue / issue_peak,
                 peak_note="FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock); executed FP32 flops per pixel "
                           "pair from ncu opcode counts; issue_frac = thread instructions per pair x pairs / time over "
@@ -377,8 +381,8 @@ def run_single(args, dist, rank, world, dev):
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         stage_ms=stage_ms,
         pairs=pairs, tile_pairs=tile_pairs, status=st,
-        roofline=roofline(dominant, dom_ms, pairs, sm_max),
-        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, sm_max),
+        roofline=roofline(dominant, dom_ms, pairs, sm_max, captured=fr.qcap > 0),
+        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, sm_max, captured=fr.qcap > 0),
         e2e=dict(value=world * npix / (e2e_ms * 1e-3) / 1e6, unit="Mpixel/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=int(launches),
