@@ -48,20 +48,20 @@ FP32_LANES_PER_SM = 128
 # workload divided by its pixel pairs).  The ALU roofline of a kernel is
 # this work over its time against the FP32 peak.
 FP32_FLOPS_PER_PAIR = {
-    "k_shade": 1171.3,               # k_shade<3, save>: keeps the bound queries
-    "k_bwd_quadrature": 1247.5,      # k_bwd_quadrature<3, saved>
+    "k_shade": 1160.3,               # k_shade<3, save>: keeps the bound queries
+    "k_bwd_quadrature": 1201.4,      # k_bwd_quadrature<3, saved>
 }
 # DRAM bytes (read + write) per pair of the same captures: the saved bound
 # queries (64 B a pair) dominate; scaled to a launch by its pixel pairs.
 DRAM_BYTES_PER_PAIR = {
-    "k_shade": 71.5,
+    "k_shade": 71.6,
     "k_bwd_quadrature": 70.6,
 }
 # Thread instructions per pair from the same captures (issue-rate view:
 # peak = SMs x 4 schedulers x 32 lanes x clock).
 THREAD_INST_PER_PAIR = {
-    "k_shade": 1776.3,
-    "k_bwd_quadrature": 1702.0,
+    "k_shade": 1764.4,
+    "k_bwd_quadrature": 1602.7,
 }
 
 

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(TPB, 2)
     const bool any = sw->n_valid != 0 && !(SAVED && sw->n_pixpairs > (unsigned long long)qcap);
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
     const float4* q_end = SAVED ? pq + (size_t)qcap * nq : nullptr;   // end of the saved queries
-    const int lane = threadIdx.x & 31;
+    const int ridx = rs_index<NK_QUAD>(threadIdx.x & 31);   // compact sum this lane reduces
     for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
         PixelCtx c = pixel_ctx(vt, ranges, P, tile);
         if (!any) c.end = c.start;
@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(TPB, 2)
                 const float* r = s_rec + k * REC;
                 const bool active = c.inside && rect_contains(r, c.px, c.py);
                 if (!__any_sync(0xffffffffu, active)) continue;
-                float acc[32];
+                float acc[NK_QUAD];
 #pragma unroll
-                for (int f = 0; f < 32; ++f) acc[f] = 0.0f;
+                for (int f = 0; f < NK_QUAD; ++f) acc[f] = 0.0f;
                 if (active) {
                     // the pixel's saved queries are contiguous in pair order: start
                     // fetching the next pair's into L2 while this one is processed
@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(TPB, 2)
                     acc[K_RGB + 1] = pa.gS[1] * po.O;
                     acc[K_RGB + 2] = pa.gS[2] * po.O;
                 }
-                const float v = reduce_scatter32(acc);
-                if (lane < NK_QUAD && v != 0.0f) atomicAdd(&s_acc[k * NK_QUAD + lane], v);
+                const float v = reduce_scatter<NK_QUAD>(acc);
+                if (ridx >= 0 && v != 0.0f) atomicAdd(&s_acc[k * NK_QUAD + ridx], v);
             }
             __syncthreads();
             flush_batch(s_rec, s_acc, nb, NK_QUAD, NGRAD, ids, c.start + b * p.batch, c.rec_base, grec);

@@ -97,9 +97,9 @@ MB_HD void sym_update_sq(float B[NB], float s, const float u[5]) {
     }
 }
 
-MB_HD float kdot(const Recon& R, const float Pa[5], const float Pb[5]) {
-    return Pa[0] * Pb[0] + R.h[0] * Pa[1] * Pb[1] + R.h[1] * Pa[2] * Pb[2] + R.h[2] * Pa[3] * Pb[3] +
-           R.h[3] * Pa[4] * Pb[4];
+// sum_k a_k b_k: with a = pi(t) and b = e(x) = (h_k pi_k(x)) it is K(t, x)
+MB_HD float dot5(const float a[5], const float b[5]) {
+    return fmaf(a[4], b[4], fmaf(a[3], b[3], fmaf(a[2], b[2], fmaf(a[1], b[1], a[0] * b[0]))));
 }
 
 // Adjoint of one bound query.  Adds gq * m0 * dF/dy (standardised y) to *gy
@@ -108,36 +108,35 @@ MB_HD float kdot(const Recon& R, const float Pa[5], const float Pb[5]) {
 // (finish_moment_adjoint).
 MB_HD void query_adjoint(const Params& p, const Recon& R, const QueryRec& q, float gq, float* gy, float B[NB]) {
     if (R.m0 <= 0.0f || gq == 0.0f) return;
-    float Py[5], Dy[5];
+    float Py[5], Dy[5], ey[5];
     pis_d(R, q.y, Py, Dy);
-    const float Kyy = kdot(R, Py, Py);
-    const float w0 = fdiv_(1.0f, Kyy);   // Kyy >= 1
-    const float K1yy = kdot(R, Dy, Py);
+    kernel_coeffs(R, Py, ey);                   // K(t, y) = sum_k ey_k pi_k(t)
+    const float Kyy = dot5(Py, ey);
+    const float w0 = fdiv_(1.0f, Kyy);          // Kyy >= 1
+    const float K1yy = dot5(Dy, ey);
     const float dw0 = -2.0f * w0 * w0 * K1yy;
     const bool left = q.j <= 2;
     const float sgn = left ? 1.0f : -1.0f;      // sign of the root weights in F
     const float c0 = left ? p.beta : -(1.0f - p.beta);
     float dF = c0 * dw0;
-    float ey[5];
-    kernel_coeffs(R, Py, ey);
     sym_update_sq(B, gq * c0 * w0 * w0, ey);
     if (!left) B[0] += gq;      // the constant 1 of F = 1 - ...
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         if (r >= q.nroot) break;
         const float x = q.x[r];
-        float Px[5], Dx[5];
+        float Px[5], Dx[5], ex[5];
         pis_d(R, x, Px, Dx);
-        const float w = fdiv_(1.0f, kdot(R, Px, Px));
+        kernel_coeffs(R, Px, ex);
+        const float w = fdiv_(1.0f, dot5(Px, ex));
         if (!isfinite(w) || w == 0.0f) continue;
-        const float K1xx = kdot(R, Dx, Px);
-        const float K1xy = kdot(R, Dx, Py);
-        const float K1yx = kdot(R, Dy, Px);
+        const float K1xx = dot5(Dx, ex);
+        const float K1xy = dot5(Dx, ey);
+        const float K1yx = dot5(Dy, ex);
         const float rho = K1xy != 0.0f ? fdiv_(K1xx, K1xy) : 0.0f;
         dF = fmaf(sgn, 2.0f * w * w * rho * K1yx, dF);
         // Phi += s (K_x^2 - 2 rho K_x K_y) = s sym(e_x (e_x - 2 rho e_y)^T)
-        float ex[5], v[5];
-        kernel_coeffs(R, Px, ex);
+        float v[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) v[k] = fmaf(-2.0f * rho, ey[k], ex[k]);
         sym_update(B, gq * sgn * w * w, ex, v);
@@ -254,6 +253,8 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
         qb = qin[1];
     }
     load_sample<SAVED>(p, R, g, isq, 0, qa, c);
+    // T_j = e^{-tau_j}, carried: T_{j+1} = T_j e^{-dtau_j} (e^{-dtau} = 1 - dtau ph)
+    float Tc = expf(-c.tau), Tn = Tc;
 #pragma unroll 1
     for (int j = 0; j <= N; ++j) {
         if (j < N) {
@@ -264,7 +265,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             const float dtr = n.tau - c.tau;
             const bool pos = dtr > 0.0f;
             const float dtau = pos ? dtr : 0.0f;
-            const float Tj = expf(-c.tau);
+            const float Tj = Tc;
             const float d0 = c.t - g.mu;
             const float e0 = c.gau;
             const float sig = g.what * e0;
@@ -282,6 +283,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
                 ph = -xm * idt;
                 dph = (1.0f + xm - ph) * idt;
             }
+            Tn = Tj * fmaf(-dtau, ph, 1.0f);
             const float term = Tj * ph * sig * Delta;
             o.O += term;
             const float tij = tscale * (n.erf - c.erf);
@@ -322,6 +324,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             o.g_Sig = fmaf(c.gt, p.kappa * p.x_nodes[j], o.g_Sig);
         }
         c = n;
+        Tc = Tn;
     }
     return o;
 }
@@ -499,22 +502,52 @@ MB_HD float expand_geometry(const float* __restrict__ r, const float* __restrict
 }
 
 #ifdef __CUDACC__
-// Warp reduce-scatter of 32 per-lane values: lane f returns the warp sum of
-// v[f] (31 shuffles instead of 32 x 5 for per-field butterflies).  All 32
-// lanes must call it.
-__device__ __forceinline__ float reduce_scatter32(float v[32]) {
-    const int lane = threadIdx.x & 31;
+// Warp reduce-scatter of M <= 32 per-lane values.  Each of 5 butterfly levels
+// halves the slots a lane holds (n -> ceil(n/2); the upper lane of a pair
+// keeps the upper part), so M = 19 takes 10 + 5 + 3 + 2 + 1 = 21 shuffles.
+// Lane L returns the warp sum of v[rs_index<M>(L)] (0 where that is -1).  All
+// 32 lanes must call it.
+template <int N, int O>
+struct ReduceScatterLevel {
+    static __device__ __forceinline__ void run(float* v, int lane) {
+        constexpr int H = (N + 1) / 2;
+        const bool up = (lane & O) != 0;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = up ? v[i] : v[i + o];
-            const float keep = up ? v[i + o] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        for (int i = 0; i < H; ++i) {
+            const float hv = (H + i < N) ? v[H + i] : 0.0f;
+            const float send = up ? v[i] : hv;
+            const float keep = up ? hv : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
         }
+        ReduceScatterLevel<H, O / 2>::run(v, lane);
     }
+};
+template <int N>
+struct ReduceScatterLevel<N, 0> {
+    static __device__ __forceinline__ void run(float*, int) {}
+};
+
+template <int M>
+__device__ __forceinline__ float reduce_scatter(float v[M]) {
+    ReduceScatterLevel<M, 16>::run(v, threadIdx.x & 31);
     return v[0];
+}
+
+// The value index a lane returns from reduce_scatter<M>, or -1.
+template <int M>
+MB_HD int rs_index(int lane) {
+    int n = M, base = 0, cnt = M;
+    for (int o = 16; o >= 1; o >>= 1) {
+        const int h = (n + 1) / 2;
+        if (lane & o) {
+            base += h;
+            cnt -= h;
+        } else {
+            cnt = cnt < h ? cnt : h;
+        }
+        n = h;
+    }
+    return cnt >= 1 ? base : -1;
 }
 
 // Warp reduction of 16 per-lane values: lanes f and f + 16 return the warp

@@ -647,6 +647,7 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
     float O = 0.0f, P = 0.0f;
     float t_prev = 0.0f, tau_prev = 0.0f, erf_prev = 0.0f;
     float gau_prev = 0.0f;
+    float T_prev = 0.0f;   // e^{-tau_prev}, carried: T_{j+1} = T_j e^{-dtau_j}
 #pragma unroll 1
     for (int j = 0; j <= N; ++j) {
         const float raw = fmaf(ks, p.x_nodes[j], g.mu);
@@ -669,14 +670,24 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
         if (j > 0) {
             const float Delta = tj - t_prev;
             const float dtau = fmaxf(tau - tau_prev, 0.0f);
-            const float Tj = expf(-tau_prev);
+            const float Tj = T_prev;
             const float sig = g.what * gau_prev;
-            const float ratio = dtau < 1e-6f ? fmaf(-0.5f, dtau, 1.0f) : fdiv_(-expm1f(-dtau), dtau);
+            float ratio, em;   // (1 - e^{-dtau}) / dtau and e^{-dtau}
+            if (dtau < 1e-6f) {
+                ratio = fmaf(-0.5f, dtau, 1.0f);
+                em = fmaf(-dtau, ratio, 1.0f);
+            } else {
+                const float xm = expm1f(-dtau);
+                ratio = fdiv_(-xm, dtau);
+                em = 1.0f + xm;
+            }
             O = fmaf(Tj * ratio, sig * Delta, O);
+            T_prev = Tj * em;
             const float tij = tscale * (erf_j - erf_prev);
             const float v = fmaxf(tij - dtau, 0.0f);
             P = fmaf(v, v, P);
         }
+        if (j == 0) T_prev = expf(-tau);
         t_prev = tj;
         tau_prev = tau;
         erf_prev = erf_j;
