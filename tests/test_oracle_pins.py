@@ -354,6 +354,39 @@ def test_quadrature_with_exact_tau_converges_to_volume_rendering():
     assert errs[-1] < 2e-3 and errs[-1] < errs[0] / 4, errs
 
 
+def _interval_integral(mu, Sig, wh, a, b):
+    """int_a^b wh exp(-(t - mu)^2 / (2 Sig^2)) dt by adaptive quadrature."""
+    return integrate.quad(lambda t: wh * math.exp(-0.5 * ((t - mu) / Sig) ** 2), a, b,
+                          epsabs=1e-14, epsrel=1e-12, points=[mu] if a < mu < b else None)[0]
+
+
+def test_penalty_and_opacity_special_cases():
+    """App. D penalty and the Eq. 7 opacity against numerical integration.
+    With the exact optical depth of all Gaussians on the ray, every interval's
+    total increase is at least Gaussian i's own share, so P_i = 0.  With
+    tau = 0, P_i = sum_j (int_{t_j}^{t_{j+1}} sigma_i)^2 and O_i is the
+    left-edge Riemann sum sum_j sigma_i(t_j) Delta_j (density at the left edge,
+    T = 1)."""
+    cfg = O.OracleConfig()
+    # (mu, Sigma, w-hat) on one ray; the last one has samples clamped to t_n,
+    # so its left- and right-edge sums differ (the nodes are symmetric)
+    g = [(2.0, 0.15, 3.0), (2.2, 0.3, 0.7), (1.7, 0.05, 12.0), (0.03, 0.02, 2.0)]
+    mu, Sig, wh = (T([x[k] for x in g]) for k in range(3))
+    t = O.sample_points(mu, Sig, cfg)                                  # (3, N+1)
+    tn = cfg.t_near
+    exact = np.array([[sum(_interval_integral(m, s_, w, tn, float(tt)) for m, s_, w in g) for tt in row]
+                      for row in t.numpy()])
+    _, P = O.quadrature(mu, Sig, wh, t, T(exact), cfg)
+    assert float(P.abs().max()) < 1e-20
+    O0, P0 = O.quadrature(mu, Sig, wh, t, torch.zeros_like(t), cfg)
+    for i, (m, s_, w) in enumerate(g):
+        ti = t[i].numpy()
+        parts = [_interval_integral(m, s_, w, ti[j], ti[j + 1]) for j in range(len(ti) - 1)]
+        assert abs(float(P0[i]) - sum(v * v for v in parts)) < 1e-12 * max(1.0, sum(v * v for v in parts))
+        riemann = sum(w * math.exp(-0.5 * ((ti[j] - m) / s_) ** 2) * (ti[j + 1] - ti[j]) for j in range(len(ti) - 1))
+        assert abs(float(O0[i]) - riemann) < 1e-12 * riemann
+
+
 def test_permutation_invariance_and_monotone_T():
     cfg = O.OracleConfig()
     sc = scenes.scene_uniform(400, 8)
