@@ -212,6 +212,25 @@ def test_discrete_measure_is_its_own_canonical_representation():
         assert abs(float(U) - wts[atoms <= eta].sum()) < 1e-8
 
 
+def test_optical_depth_interpolates_the_bounds_with_beta():
+    """Eq. 8 with the printed beta: for an unbiased 5-atom measure of mass m0
+    queried at an atom, L and U are the masses strictly below / up to the atom,
+    so tau = m0 (L + beta w_atom)."""
+    beta = json.load(open(GOLD))["beta"]["value"]
+    cfg = O.OracleConfig(bias_alpha=0.0)
+    assert cfg.beta == beta
+    rng = np.random.default_rng(12)
+    for _ in range(10):
+        atoms = np.sort(rng.uniform(0.05, 0.95, 5))
+        wts = rng.uniform(0.05, 1.0, 5)
+        wts /= wts.sum()
+        m0 = rng.uniform(0.5, 8.0)
+        i = int(rng.integers(0, 5))
+        m = T([m0 * (wts * atoms ** k).sum() for k in range(9)])
+        tau = float(O.optical_depth(m[None], T([[atoms[i]]]), cfg))
+        assert abs(tau - m0 * (wts[:i].sum() + beta * wts[i])) < 1e-7 * m0
+
+
 @pytest.mark.parametrize("n", [2, 3, 4])
 def test_canonical_matches_independent_nonlinear_solve(n):
     """Independent pin: solve sum_i w_i x_i^k = b_k (k = 0..2n) for n free atoms
@@ -385,6 +404,16 @@ def test_penalty_and_opacity_special_cases():
         assert abs(float(P0[i]) - sum(v * v for v in parts)) < 1e-12 * max(1.0, sum(v * v for v in parts))
         riemann = sum(w * math.exp(-0.5 * ((ti[j] - m) / s_) ** 2) * (ti[j + 1] - ti[j]) for j in range(len(ti) - 1))
         assert abs(float(O0[i]) - riemann) < 1e-12 * riemann
+    # an optical depth that decreases along the ray counts as no increase
+    # (dtau clamped at 0): T_j weights the left-edge sum, the penalty is that of tau = 0
+    tdec = 2.0 - 0.1 * torch.arange(t.shape[-1], dtype=DT).expand_as(t)
+    Od, Pd = O.quadrature(mu, Sig, wh, t, tdec, cfg)
+    for i, (m, s_, w) in enumerate(g):
+        ti = t[i].numpy()
+        ref = sum(math.exp(-float(tdec[i, j])) * w * math.exp(-0.5 * ((ti[j] - m) / s_) ** 2) * (ti[j + 1] - ti[j])
+                  for j in range(len(ti) - 1))
+        assert abs(float(Od[i]) - ref) < 1e-12 * ref
+        assert abs(float(Pd[i]) - float(P0[i])) < 1e-15
 
 
 def test_permutation_invariance_and_monotone_T():
@@ -418,6 +447,7 @@ def test_proxy_boundary_is_the_confidence_level_set():
     pre = O.preprocess(sc, cam, cfg)
     _, _, Kinv, _ = O.camera_tensors(cam)
     idx = torch.nonzero(pre.visible & ~pre.full)[:20, 0]
+    assert len(idx) == 20
     for i in idx.tolist():
         W = pre.extra["W"][i]
         W22inv = torch.linalg.inv(W[:2, :2])
@@ -458,6 +488,47 @@ def test_proxy_rect_contains_ellipse_interior():
                 assert x0 - 1 <= px <= x1 + 1 and y0 - 1 <= py <= y1 + 1
 
 
+def test_proxy_rect_is_the_pixel_centres_in_the_ellipse_box():
+    """G17: a pixel contributes iff its centre (x + 1/2, y + 1/2) lies in the
+    closed axis-aligned box of the proxy ellipse.  The box is measured from
+    points on the ellipse W (p_hom^T W p_hom = 0) found by root bracketing
+    along rays from its centre, not from Sigma_2d."""
+    cfg = O.OracleConfig()
+    sc = scenes.scene_uniform(300, 10)
+    cam = scenes.look_at((0, 0, -3), width=96, height=80)
+    pre = O.preprocess(sc, cam, cfg)
+    idx = torch.nonzero(pre.visible & ~pre.full)[:25, 0].tolist()
+    assert len(idx) == 25
+    checked = 0
+    for i in idx:
+        W = pre.extra["W"][i].numpy()
+        c = pre.mu2d[i].numpy()
+        q = lambda p: float(np.array([p[0], p[1], 1.0]) @ W @ np.array([p[0], p[1], 1.0]))
+        assert q(c) > 0                                     # the centre is inside
+        xs, ys = [], []
+        for th in np.linspace(0.0, 2 * np.pi, 721)[:-1]:
+            d = np.array([math.cos(th), math.sin(th)])
+            hi = 1.0
+            while q(c + hi * d) > 0:
+                hi *= 2.0
+            r = optimize.brentq(lambda s_: q(c + s_ * d), 0.0, hi, xtol=1e-12)
+            xs.append(c[0] + r * d[0])
+            ys.append(c[1] + r * d[1])
+        lo = np.array([min(xs), min(ys)])
+        hi_ = np.array([max(xs), max(ys)])
+        x0, y0, x1, y1 = pre.rect[i].tolist()
+        for axis, (a, b), size in [(0, (x0, x1), cam.width), (1, (y0, y1), cam.height)]:
+            centres = np.arange(size) + 0.5
+            inside = np.nonzero((centres >= lo[axis] - 1e-4) & (centres <= hi_[axis] + 1e-4))[0]
+            sure = np.nonzero((centres >= lo[axis] + 1e-4) & (centres <= hi_[axis] - 1e-4))[0]
+            if len(sure) == 0:
+                continue
+            assert a <= sure[0] and b >= sure[-1], (i, axis)
+            assert a >= inside[0] and b <= inside[-1], (i, axis)
+            checked += 1
+    assert checked >= 25
+
+
 def test_frustum_culling():
     cfg = O.OracleConfig()
     cam = scenes.look_at((0, 0, -3), width=64, height=64, fov_deg=60)
@@ -470,6 +541,32 @@ def test_frustum_culling():
     # a Gaussian whose peak density never reaches the confidence constant C is culled
     sc.weights[0] = 0.5 * float(pre.extra["C"][0])
     assert O.preprocess(sc, cam, cfg).visible.tolist() == [False, False, False, False]
+
+
+def test_culling_sphere_radius_and_near_bound():
+    """Sec. 3.3 / G16: the bounding sphere has radius r_mult max(s) (3 max(s)).
+    Centres 2 max(s) and 4 max(s) outside the left frustum plane: kept and
+    culled.  A sphere wholly within t_n of the camera is culled; one that
+    reaches past t_n is kept."""
+    cfg = O.OracleConfig()
+    assert cfg.r_mult == 3.0
+    cam = scenes.look_at((0, 0, -3), width=64, height=64, fov_deg=60)
+    Rv, tv, _, _ = O.camera_tensors(cam)
+    s = 0.01
+    Z = 3.0
+    nrm = math.hypot(cam.fx, cam.cx)
+    pts_cam = []
+    for k in (2.0, 4.0):                                  # distance k*s beyond the plane fx X + cx Z = 0
+        X = (-cam.cx * Z - k * s * nrm) / cam.fx
+        pts_cam.append([X, 0.0, Z])
+    pts_cam += [[0.0, 0.0, 0.004], [0.0, 0.0, 0.012]]     # near bound: r = 3e-3, t_n = 0.01
+    sizes = [s, s, 0.001, 0.001]
+    means = np.array([(Rv.T @ (T(p) - tv)).numpy() for p in pts_cam], np.float32)
+    P = len(means)
+    sc = scenes.Scene(means, np.array([[z, z, z] for z in sizes], np.float32),
+                      np.tile(np.array([1, 0, 0, 0], np.float32), (P, 1)), np.full(P, 50.0, np.float32),
+                      np.zeros((P, 1, 3), np.float32), 0)
+    assert O.preprocess(sc, cam, cfg).visible.tolist() == [True, False, False, True]
 
 
 def test_sh_basis_matches_scipy():
