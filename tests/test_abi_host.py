@@ -79,3 +79,41 @@ def test_multiview_tiles(lib):
     from paper_2512_11800_gb300 import _binding as B
     cams = (B.Camera * 3)(_cam(640, 360), _cam(1280, 720), _cam(1920, 1080))
     assert lib.mb3dgs_num_tiles(None, cams, 3) == 40 * 23 + 80 * 45 + 120 * 68
+
+
+def test_execution_shape_validation_and_tile_counts(lib):
+    """Tile shapes w x h with w in {8, 16, 32, 64} and w h = 256 threads,
+    record batches that are multiples of 32 up to 256, two schedules; the
+    tile count follows the shape (ragged last row and column)."""
+    from paper_2512_11800_gb300 import _binding as B
+    cam = _cam(131, 77)
+    n = C.c_size_t(0)
+    for tw, th in [(8, 32), (16, 16), (32, 8), (64, 4)]:
+        c = B.Config()
+        lib.mb3dgs_config_default(C.byref(c))
+        c.tile_w, c.tile_h = tw, th
+        assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 10, 0, C.byref(n)) == 0
+        assert lib.mb3dgs_num_tiles(C.byref(c), C.byref(cam), 1) == ((131 + tw - 1) // tw) * ((77 + th - 1) // th)
+    for tw, th, batch, sched, code in [(16, 8, 256, 0, -6), (24, 16, 256, 0, -6), (128, 2, 256, 0, -6),
+                                       (16, 16, 48, 0, -6), (16, 16, 512, 0, -6), (16, 16, 64, 7, -1)]:
+        c = B.Config()
+        lib.mb3dgs_config_default(C.byref(c))
+        c.tile_w, c.tile_h, c.batch, c.schedule = tw, th, batch, sched
+        assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 10, 0, C.byref(n)) == code, (tw, th, batch)
+
+
+def test_query_capacity_policy():
+    """Saved queries (16 B x (N+1) a pair) only while they fit the budget and
+    stay below 2^31 pairs; otherwise the backward recomputes them (0)."""
+    from paper_2512_11800_gb300 import RasterConfig, Rasterizer
+    R = Rasterizer(RasterConfig(query_budget_gb=1.0))
+    per_pair = 16 * (R.config.n_intervals + 1)
+    fit = (1 << 30) // per_pair
+    assert R.set_query_capacity(fit) == fit
+    assert R.set_query_capacity(fit + 1) == 0
+    assert R.set_query_capacity(0) == 0
+    R.config.query_budget_gb = 1e6
+    assert R.set_query_capacity(2 ** 31 - 1) == 2 ** 31 - 1
+    assert R.set_query_capacity(2 ** 31) == 0
+    R.config.save_queries = False
+    assert R.set_query_capacity(1000) == 0
