@@ -1,4 +1,4 @@
-"""CPU regression guard for the CUDA path's forward arithmetic.
+"""CPU regression guard for the CUDA path's forward and backward arithmetic.
 
 tests/host/emulate_forward.cu compiles the device functions of the forward
 (preprocess_one, pair_gaussian, legendre_moments, reconstruct_pixel,
@@ -6,6 +6,10 @@ pair_quadrature, the Eq. 15 epilogue) for the host.  The emulation runs them
 per pixel over the Gaussians whose rectangle holds the pixel centre, in
 ascending id order as the kernels do, and is compared with the FP64 oracle at
 the parity bar (1e-4 on RGB and final transmittance).
+tests/host/emulate_backward.cu does the same for the two adjoint passes and
+the preprocessing adjoint (saved and recomputed bound queries).  It is
+compared with the oracle gradient at the backward bar (relative L2 1e-3 per
+parameter group).
 
 This is a guard, not the parity evidence.  Host libm replaces the device's
 exp and erf, division is exact, and binning, tiling and launches are not
@@ -35,21 +39,29 @@ def _nvcc():
     return None
 
 
-@pytest.fixture(scope="module")
-def emulator(tmp_path_factory):
+def _compile(tmp_path_factory, name):
     nvcc = _nvcc()
     if nvcc is None:
         pytest.skip("nvcc not available")
-    exe = str(tmp_path_factory.mktemp("emu") / "emulate_forward")
+    exe = str(tmp_path_factory.mktemp("emu") / name)
     cmd = [nvcc, "-O2", "-std=c++17", "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"),
-           "-gencode", "arch=compute_103a,code=sm_103a", os.path.join(HERE, "host", "emulate_forward.cu"), "-o", exe]
+           "-gencode", "arch=compute_103a,code=sm_103a", os.path.join(HERE, "host", name + ".cu"), "-o", exe]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-2000:]
     return exe
 
 
-def emulate(exe, tmp, sc, cam, region):
-    fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
+@pytest.fixture(scope="module")
+def emulator(tmp_path_factory):
+    return _compile(tmp_path_factory, "emulate_forward")
+
+
+@pytest.fixture(scope="module")
+def emulator_bwd(tmp_path_factory):
+    return _compile(tmp_path_factory, "emulate_backward")
+
+
+def _write_input(fin, sc, cam, region, extra=()):
     with open(fin, "wb") as f:
         f.write(struct.pack("<qi", sc.P, sc.sh_degree))
         for a in [sc.means, sc.scales, sc.quats, sc.weights, sc.sh]:
@@ -57,6 +69,13 @@ def emulate(exe, tmp, sc, cam, region):
         f.write(np.asarray(cam.viewmat, np.float32).tobytes())
         f.write(struct.pack("<ffffii", cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height))
         f.write(struct.pack("<4i", *region))
+        for a in extra:
+            f.write(np.ascontiguousarray(a, np.float32).tobytes())
+
+
+def emulate(exe, tmp, sc, cam, region):
+    fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
+    _write_input(fin, sc, cam, region)
     subprocess.run([exe, fin, fout], check=True, timeout=600)
     w, h = region[2], region[3]
     d = np.fromfile(fout, np.float32).astype(np.float64)
@@ -92,3 +111,35 @@ def test_host_emulated_forward_matches_oracle(emulator, tmp_path, name):
     e_T = float(np.abs(T - ref["T"].numpy()).max())
     assert np.isfinite(rgb).all() and np.isfinite(T).all()
     assert e_rgb <= TOL and e_T <= TOL, (name, e_rgb, e_T)
+
+
+NAMES = ["means", "scales", "quats", "weights", "sh"]
+
+
+@pytest.mark.parametrize("mode", ["saved", "recomputed"])
+@pytest.mark.parametrize("name", ["uniform2k_full", "sh3_near_camera"])
+def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, name, mode):
+    if name == "sh3_near_camera":
+        sc = scenes.tiny_scene(P=40, seed=9, deg=3, spread=0.5)
+        cam = scenes.look_at((0.1, 0.2, -2.0), width=48, height=40, fov_deg=55)
+    else:
+        sc, cam = scenes.workload("uniform2k_128")
+    region = (0, 0, cam.width, cam.height)
+    rng = np.random.default_rng(0)
+    g_img = rng.normal(size=(cam.height, cam.width, 3))
+    gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_input(fin, sc, cam, region, extra=(g_img, gP_img))
+    subprocess.run([emulator_bwd, fin, fout, mode], check=True, timeout=900)
+    d = np.fromfile(fout, np.float32).astype(np.float64)
+    shapes = [sc.means.shape, sc.scales.shape, sc.quats.shape, sc.weights.shape, sc.sh.shape]
+    got, o = {}, 0
+    for k, shp in zip(NAMES, shapes):
+        n = int(np.prod(shp))
+        got[k] = d[o:o + n]
+        o += n
+    assert o == d.size
+    ref = O.render_grad(sc, cam, oracle_config(), g_img, gP_img)
+    err = {k: float(np.linalg.norm(got[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
+    print("host-emulated backward rel-L2", name, mode, {k: "%.2e" % v for k, v in err.items()})
+    assert max(err.values()) <= 1e-3, (name, mode, err)
