@@ -91,7 +91,8 @@ typedef struct mb3dgs_config {
     int batch;
     int schedule;
     int64_t query_capacity; /* (pixel, Gaussian) pair slots in which mb3dgs_shade keeps
-                           the N+1 bound queries of every pair (64 bytes a pair) for
+                           the N+1 bound queries of every pair (16 (N+1) bytes a
+                           pair: 64 at N = 3) for
                            mb3dgs_backward; 0 (default): backward recomputes them.
                            Size it with the pixel-pair count of
                            mb3dgs_get_pair_counts; a frame with more pairs sets
