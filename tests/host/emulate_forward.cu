@@ -1,15 +1,17 @@
 // Host build of the CUDA path's per-pixel forward arithmetic, for the CPU
 // regression test (tests/test_host_emulation.py).  It runs the same device
 // functions (preprocess_one, pair_gaussian, legendre_moments,
-// reconstruct_pixel, pair_quadrature, the Eq. 15 epilogue) compiled for the
-// host, with the host's libm for exp/erf and exact division in place of the
+// reconstruct_pixel, pair_quadrature, the Eq. 15 epilogue, and the
+// transmittance query optical_depth) compiled for the host, with the host's libm for exp/erf and exact division in place of the
 // approximate one.  It covers the arithmetic only: binning, tiling,
 // scheduling and every kernel launch are left out (contributing Gaussians are
 // found by rectangle tests).
 //
-// stdin-free: argv[1] = input file (int64 P, int32 sh_degree, float32 SoA
-// means, scales, quats, weights, sh, mb3dgs_camera, int32 region x0 y0 w h),
-// argv[2] = output file (float32 rgb [h][w][3], T [h][w]).
+// argv[1] = input file (int64 P, int32 sh_degree, float32 SoA means, scales,
+// quats, weights, sh, mb3dgs_camera, int32 region x0 y0 w h), argv[2] =
+// output file (float32 rgb [h][w][3], T [h][w], T(eta_q) [h][w][17] at the
+// warped depths eta_q = q/16), argv[3] (optional) = N intervals (default 3;
+// other values run the runtime-N template).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -43,7 +45,7 @@ static void rd(FILE* f, T* x, size_t n) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 3) return 2;
+    if (argc != 3 && argc != 4) return 2;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
     int64_t P;
@@ -64,6 +66,7 @@ int main(int argc, char** argv) {
     fclose(f);
     mb3dgs_config cfg;
     mb3dgs_config_default(&cfg);
+    if (argc == 4) cfg.n_intervals = atoi(argv[3]);
     Params p;
     make_params(&cfg, p);
     ViewTable vt;
@@ -81,7 +84,8 @@ int main(int argc, char** argv) {
         const int* ri = reinterpret_cast<const int*>(&rec[i * REC + R_RECT]);
         if (ri[0] <= ri[2] && ri[2] >= x0 && ri[0] < x0 + W && ri[3] >= y0 && ri[1] < y0 + H) list.push_back(i);
     }
-    std::vector<float> out_rgb(3 * W * H), out_T(W * H);
+    constexpr int NPROBE = 17;
+    std::vector<float> out_rgb(3 * W * H), out_T(W * H), out_probe(NPROBE * W * H);
     for (int q = 0; q < W * H; ++q) {
         const int px = x0 + q % W, py = y0 + q / W;
         const float ux = ((float)px + 0.5f - V.cx) / V.fx, uy = ((float)py + 0.5f - V.cy) / V.fy;
@@ -100,18 +104,21 @@ int main(int argc, char** argv) {
             const float* r = &rec[i * REC];
             if (!rect_contains(r, px, py)) continue;
             const Gauss1D g = pair_gaussian(r, (float)px + 0.5f - r[R_AX], (float)py + 0.5f - r[R_AY], rl, r2);
-            const float Oi = pair_quadrature<3>(p, R, g, &Pen);
+            const float Oi = p.n_intervals == 3 ? pair_quadrature<3>(p, R, g, &Pen) : pair_quadrature<0>(p, R, g, &Pen);
             for (int c = 0; c < 3; ++c) S[c] += r[R_RGB + c] * Oi;
             O += Oi;
         }
         const float m0 = acc[0], Tf = expf(-m0), sc = -expm1f(-m0) / fmaxf(p.eps, O);
         for (int c = 0; c < 3; ++c) out_rgb[3 * q + c] = sc * S[c] + Tf * p.bg[c];
         out_T[q] = Tf;
+        for (int k = 0; k < NPROBE; ++k)
+            out_probe[q * NPROBE + k] = expf(-optical_depth(R, p.beta, 2.0f * ((float)k / 16.0f) - 1.0f));
     }
     FILE* o = fopen(argv[2], "wb");
     if (!o) return 2;
     fwrite(out_rgb.data(), 4, out_rgb.size(), o);
     fwrite(out_T.data(), 4, out_T.size(), o);
+    fwrite(out_probe.data(), 4, out_probe.size(), o);
     fclose(o);
     return 0;
 }
