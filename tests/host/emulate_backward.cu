@@ -9,7 +9,8 @@
 // The per-record sums are plain host sums in place of the warp, shared-memory
 // and global reductions; binning, tiling and launches are left out.  With
 // argv[3] == "saved" the bound queries kept by the forward feed pass 1, else
-// pass 1 solves them again.
+// pass 1 solves them again.  argv[4] (optional): N intervals (default 3; other
+// values run the runtime-N templates).
 //
 // argv[1]: input file (as for emulate_forward, then float32 dL/drgb [h][w][3]
 // and dL/dP [h][w] of the region); argv[2]: output file (float32 gradients of
@@ -47,7 +48,7 @@ static void rd(FILE* f, T* x, size_t n) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 4) return 2;
+    if (argc != 4 && argc != 5) return 2;
     const bool saved = strcmp(argv[3], "saved") == 0;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
@@ -73,6 +74,7 @@ int main(int argc, char** argv) {
     fclose(f);
     mb3dgs_config cfg;
     mb3dgs_config_default(&cfg);
+    if (argc == 5) cfg.n_intervals = atoi(argv[4]);
     Params p;
     make_params(&cfg, p);
     ViewTable vt;
@@ -112,7 +114,8 @@ int main(int argc, char** argv) {
         for (size_t k = 0; k < mine.size(); ++k) {
             const float* r = &rec[mine[k] * REC];
             const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], rl, r2);
-            const float Oi = pair_quadrature<3, true>(p, R, g, &Pen, &qs[k * nq]);
+            const float Oi = p.n_intervals == 3 ? pair_quadrature<3, true>(p, R, g, &Pen, &qs[k * nq])
+                                                : pair_quadrature<0, true>(p, R, g, &Pen, &qs[k * nq]);
             for (int c = 0; c < 3; ++c) S[c] += r[R_RGB + c] * Oi;
             O += Oi;
         }
@@ -126,8 +129,13 @@ int main(int argc, char** argv) {
             const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
             const Gauss1D g = pair_gaussian(r, dx, dy, rl, r2);
             const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
-            const PairOut po = saved ? pair_backward<3, true>(p, R, g, a, pa.gP, B, &qs[k * nq])
-                                     : pair_backward<3, false>(p, R, g, a, pa.gP, B);
+            PairOut po;
+            if (p.n_intervals == 3)
+                po = saved ? pair_backward<3, true>(p, R, g, a, pa.gP, B, &qs[k * nq])
+                           : pair_backward<3, false>(p, R, g, a, pa.gP, B);
+            else
+                po = saved ? pair_backward<0, true>(p, R, g, a, pa.gP, B, &qs[k * nq])
+                           : pair_backward<0, false>(p, R, g, a, pa.gP, B);
             float c[NK_QUAD];
             for (int f2 = 0; f2 < NK_QUAD; ++f2) c[f2] = 0.0f;
             geometry_adjoint_compact(r, dx, dy, rl, g, po.g_mu, po.g_Sig, po.g_what, c);

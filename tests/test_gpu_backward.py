@@ -81,6 +81,21 @@ def test_backward_sh3_near_camera(R):
     assert max(err.values()) <= REL, err
 
 
+def test_backward_other_interval_count(R):
+    """N = 5 runs the runtime-N adjoint kernels (k_bwd_quadrature<0, ...>)."""
+    from paper_2512_11800_gb300 import RasterConfig, Rasterizer
+    R5 = Rasterizer(RasterConfig(bg=(0.1, 0.2, 0.3), n_intervals=5, save_queries=R.config.save_queries))
+    sc = scenes.tiny_scene(P=40, seed=9, deg=3, spread=0.5)
+    cam = scenes.look_at((0.1, 0.2, -2.0), width=48, height=40, fov_deg=55)
+    rng = np.random.default_rng(1)
+    g_img = rng.normal(size=(cam.height, cam.width, 3))
+    gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
+    gg = gpu_grads(R5, sc, cam, g_img, gP_img)
+    ref = oracle_grad("sh3_near_N5", sc, cam, oracle_config(R5.config), g_img, gP_img)
+    err = rel_errors(gg, ref)
+    assert max(err.values()) <= REL, err
+
+
 def test_backward_full_size_crop():
     """1M Gaussians at 1920x1080 rendered and differentiated in full; the
     upstream gradient is non-zero on a 32x32 crop only, where the oracle

@@ -138,9 +138,10 @@ NAMES = ["means", "scales", "quats", "weights", "sh"]
 
 
 @pytest.mark.parametrize("mode", ["saved", "recomputed"])
-@pytest.mark.parametrize("name", ["uniform2k_full", "sh3_near_camera"])
+@pytest.mark.parametrize("name", ["uniform2k_full", "sh3_near_camera", "sh3_near_camera_N5", "sh3_near_camera_N1"])
 def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, name, mode):
-    if name == "sh3_near_camera":
+    N = 5 if name.endswith("N5") else (1 if name.endswith("N1") else 3)
+    if name.startswith("sh3_near_camera"):
         sc = scenes.tiny_scene(P=40, seed=9, deg=3, spread=0.5)
         cam = scenes.look_at((0.1, 0.2, -2.0), width=48, height=40, fov_deg=55)
     else:
@@ -151,7 +152,7 @@ def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, 
     gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     _write_input(fin, sc, cam, region, extra=(g_img, gP_img))
-    subprocess.run([emulator_bwd, fin, fout, mode], check=True, timeout=900)
+    subprocess.run([emulator_bwd, fin, fout, mode, str(N)], check=True, timeout=900)
     d = np.fromfile(fout, np.float32).astype(np.float64)
     shapes = [sc.means.shape, sc.scales.shape, sc.quats.shape, sc.weights.shape, sc.sh.shape]
     got, o = {}, 0
@@ -160,7 +161,7 @@ def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, 
         got[k] = d[o:o + n]
         o += n
     assert o == d.size
-    ref = O.render_grad(sc, cam, oracle_config(), g_img, gP_img)
+    ref = O.render_grad(sc, cam, oracle_config(n_intervals=N), g_img, gP_img)
     err = {k: float(np.linalg.norm(got[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
     print("host-emulated backward rel-L2", name, mode, {k: "%.2e" % v for k, v in err.items()})
     assert max(err.values()) <= 1e-3, (name, mode, err)
