@@ -117,3 +117,16 @@ def test_query_capacity_policy():
     assert R.set_query_capacity(2 ** 31) == 0
     R.config.save_queries = False
     assert R.set_query_capacity(1000) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libmb3dgs.so the loader and the Rasterizer raise."""
+    from paper_2512_11800_gb300 import RasterConfig, Rasterizer
+    from paper_2512_11800_gb300 import _binding as B
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B._build, "LIB", str(tmp_path / "missing" / "libmb3dgs.so"))
+    monkeypatch.setattr(B._build, "build", lambda *a, **k: None)     # as if the build produced nothing
+    with pytest.raises(ImportError):
+        B.load()
+    with pytest.raises(ImportError):
+        Rasterizer(RasterConfig())
