@@ -238,9 +238,10 @@ int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians*
  * in the space left after the per-Gaussian and per-pixel buffers).
  * Returns MB3DGS_ERR_WORKSPACE_TOO_SMALL, before launching anything, when the
  * Gaussians, views and pixels alone need more than the fixed size.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call uses the same array: calls that overlap on the GPU
+ * The first call on a device looks up the array's device address (with that
+ * device current) and keeps it for the device's CUDA context; after a
+ * cudaDeviceReset the next call looks it up again.  Make the first call on a
+ * device (and the first after a reset) before any stream capture.  Every call uses the same array: calls that overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the caller.
  * Allocates nothing (no cudaMalloc / cudaFree). */
 int mb3dgs_render_noalloc(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,

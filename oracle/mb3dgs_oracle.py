@@ -18,8 +18,7 @@ Eq. 7 (quadrature, App. B), Eq. 8 (moment bounds, Sec. 3.2), Eq. 10-12
 (confidence-interval proxy, App. C "Rasterisation"), consistency penalty
 (Sec. 3.4, App. D "Regularisation").
 
-Readings adopted where the paper is silent or garbled (all listed in the
-design notes): power transform of Barron (2025), f(x) = |l-1|/l * ((x/|l-1|
+Readings adopted where the paper is silent or garbled: power transform of Barron (2025), f(x) = |l-1|/l * ((x/|l-1|
 + 1)^l - 1) with l = -1.5 applied to 2t; near bound t_n = 0.01, far bound
 t_f = 1e6 (moments use the t_f -> inf closed forms); boundary term of the
 recurrence with a "+" sign and the linearised distance u_n (the appendix
@@ -470,19 +469,21 @@ def pairs_in_region(rect, x0, y0, w, h):
 # full forward for one camera
 # ----------------------------------------------------------------------------
 def render(scene, cam, cfg: OracleConfig = None, region=None, params=None, probes=None,
-           requires_grad=False, chunk=200_000, tau_fn=None):
+           requires_grad=False, chunk=200_000, tau_fn=None, pre=None):
     """Render the pixel region (x0, y0, w, h) (default: the full image).
 
     Returns a dict with rgb (h,w,3), T (h,w) = e^{-m0}, P (h,w) penalty,
     m (h,w,2n+1) moments, O (h,w), S (h,w,3) = sum_i L_i, n_pairs, and
     tau_probe (h,w,Q) = tau(eta) at the probe depths (if ``probes`` given).
     ``tau_fn(pix_index, t)`` replaces the moment-based optical depth (used by
-    the exact-tau quadrature pin)."""
+    the exact-tau quadrature pin).  ``pre`` reuses the result of
+    ``preprocess(scene, cam, cfg)`` for the same inputs (no gradient)."""
     cfg = cfg or OracleConfig()
     if region is None:
         region = (0, 0, cam.width, cam.height)
     x0, y0, w, h = region
-    pre = preprocess(scene, cam, cfg, params=params)
+    if pre is None or params is not None:
+        pre = preprocess(scene, cam, cfg, params=params)
     g, px, py = pairs_in_region(pre.rect, x0, y0, w, h)
     pix = (py - y0) * w + (px - x0)
     npix = w * h

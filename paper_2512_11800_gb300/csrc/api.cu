@@ -583,16 +583,53 @@ int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams,
 namespace mb {
 static __device__ __align__(256) unsigned char g_noalloc_ws[MB3DGS_NOALLOC_WORKSPACE_BYTES];
 
+// The device address of the array belongs to the CUDA context that loaded the
+// module: a cudaDeviceReset (or a primary context torn down and created again)
+// gives the array a new address.  So the address is cached per device together
+// with the unique id of the context it was looked up in (cuCtxGetId, reached
+// through the runtime's driver entry points, no link against libcuda), and
+// looked up again when the current context's id differs.  Without those entry
+// points it is looked up on every call.
+typedef int (*ctx_get_current_fn)(void**);
+typedef int (*ctx_get_id_fn)(void*, unsigned long long*);
+
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_ptr[256] = {};
+static unsigned long long g_noalloc_ctx[256] = {};
 
-// Device address of the static workspace for the current device; looked up once
-// per device (the array's host-side name is only a stand-in, not a device address).
+static bool current_context_id(unsigned long long* id) {
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f0 = nullptr;
+        void* f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q0 == cudaDriverEntryPointSuccess && q1 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<ctx_get_current_fn>(f0);
+            get_id = reinterpret_cast<ctx_get_id_fn>(f1);
+        }
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id) return false;
+    void* ctx = nullptr;
+    if (get_current(&ctx) != 0 || ctx == nullptr) return false;   // no context yet: the lookup creates it
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of the static workspace in the current device's context (the
+// array's host-side name is only a stand-in, not a device address).  Called
+// with the device current; the first call in a context looks the address up.
 static int noalloc_workspace(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return MB3DGS_ERR_CUDA;
+    unsigned long long ctx = 0;
+    const bool have_id = current_context_id(&ctx);
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (!have_id || !g_noalloc_ptr[dev] || g_noalloc_ctx[dev] != ctx) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
         if (e != cudaSuccess || p == nullptr) {
@@ -600,6 +637,7 @@ static int noalloc_workspace(void** out) {
             return MB3DGS_ERR_CUDA;
         }
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = have_id ? ctx : 0;
     }
     *out = g_noalloc_ptr[dev];
     return MB3DGS_OK;
@@ -621,7 +659,11 @@ extern "C" int mb3dgs_render_noalloc(const mb3dgs_config* cfg, const mb3dgs_gaus
     rc = make_layout(cfg, vt, npix, nt, g->P, 0, L);
     if (rc) return rc;
     if (L.total > cap_bytes) return MB3DGS_ERR_WORKSPACE_TOO_SMALL;   // P / pixels beyond the fixed maximum
-    // largest pair capacity whose layout still fits the static array
+    // Largest pair capacity whose layout still fits the static array.  Every
+    // region of the layout grows with the capacity or does not depend on it
+    // (pair keys and values, radix histograms), so the total is non-decreasing
+    // in the capacity and the fitting capacities form a prefix [0, lo]: a
+    // bisection over 31 bits finds its end (host arithmetic only).
     int64_t lo = 0, hi = (int64_t(1) << 31) - 1;
     while (lo < hi) {
         const int64_t mid = lo + (hi - lo + 1) / 2;

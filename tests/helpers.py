@@ -1,8 +1,11 @@
 """Shared test helpers: map the CUDA path's float32 configuration onto the
-oracle's (the oracle consumes exactly the same float32 input values)."""
+oracle's (the oracle consumes exactly the same float32 input values), and
+keep the oracle's expensive results for the large workloads once per test
+session (scene draws, FP64 preprocessing of 1M-3M Gaussians, crop renders)."""
 import numpy as np
 
 import oracle as O
+import scenes
 
 FLOAT_FIELDS = ["kappa", "beta", "conf_c", "warp_lambda", "t_near", "t_far", "eps", "bias_alpha", "m_min", "r_mult"]
 
@@ -19,3 +22,51 @@ def oracle_config(rc=None, **over):
     kw.update(n=rc.n, n_intervals=rc.n_intervals, bg=tuple(f32(b) for b in rc.bg))
     kw.update(over)
     return O.OracleConfig(**kw)
+
+
+_WORKLOADS = {}
+_PRE = {}
+_REFS = {}
+
+
+def workload(name):
+    """scenes.workload(name), drawn once per session; the arrays are made
+    read-only so that no test can change a scene another test reuses."""
+    if name not in _WORKLOADS:
+        sc, cam = scenes.workload(name)
+        for k in ["means", "scales", "quats", "weights", "sh"]:
+            getattr(sc, k).setflags(write=False)
+        _WORKLOADS[name] = (sc, cam)
+    return _WORKLOADS[name]
+
+
+def _cfg_key(cfg):
+    return tuple(sorted((k, v) for k, v in vars(cfg).items()))
+
+
+def oracle_pre(name, cfg):
+    key = (name, _cfg_key(cfg))
+    if key not in _PRE:
+        sc, cam = workload(name)
+        _PRE[key] = O.preprocess(sc, cam, cfg)
+    return _PRE[key]
+
+
+def oracle_crop(name, region, cfg=None):
+    """O.render of one pixel region of a named workload, computed once per
+    session and shared by every test that checks that region."""
+    cfg = cfg or oracle_config()
+    key = (name, tuple(region), _cfg_key(cfg))
+    if key not in _REFS:
+        sc, cam = workload(name)
+        _REFS[key] = O.render(sc, cam, cfg, region=region, pre=oracle_pre(name, cfg))
+    return _REFS[key]
+
+
+def crops(cam, seed, n, size):
+    """The centre crop and n seeded crops of size x size pixels."""
+    rng = np.random.default_rng(seed)
+    out = [((cam.width - size) // 2, (cam.height - size) // 2, size, size)]
+    for _ in range(n):
+        out.append((int(rng.integers(0, cam.width - size)), int(rng.integers(0, cam.height - size)), size, size))
+    return out

@@ -130,3 +130,32 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         B.load()
     with pytest.raises(ImportError):
         Rasterizer(RasterConfig())
+
+
+def test_workspace_size_is_monotone_in_pair_capacity(lib):
+    """The allocation-free render finds the largest pair capacity that fits
+    its fixed workspace by bisection, which needs the workspace size to be
+    non-decreasing in the pair capacity."""
+    import numpy as np
+    from paper_2512_11800_gb300 import _binding as B
+    c = B.Config()
+    lib.mb3dgs_config_default(C.byref(c))
+    cam = _cam(128, 128)
+    n = C.c_size_t(0)
+    caps = sorted(set([0, 1, 2, 3, 4095, 4096, 4097] + list(np.random.default_rng(0).integers(0, 1 << 30, 200))))
+    sizes = []
+    for cap in caps:
+        assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 2000, int(cap), C.byref(n)) == 0
+        sizes.append(n.value)
+    assert all(a <= b for a, b in zip(sizes, sizes[1:]))
+    # the largest capacity below a byte budget: it fits and the next one does not
+    budget = 64 << 20
+
+    def fits(cap):
+        assert lib.mb3dgs_workspace_size(C.byref(c), C.byref(cam), 1, 2000, cap, C.byref(n)) == 0
+        return n.value <= budget
+    lo, hi = 0, (1 << 31) - 1
+    while lo < hi:
+        mid = lo + (hi - lo + 1) // 2
+        lo, hi = (mid, hi) if fits(mid) else (lo, mid - 1)
+    assert fits(lo) and not fits(lo + 1)

@@ -12,6 +12,7 @@ import torch
 
 import oracle as O
 import scenes
+import helpers
 from helpers import oracle_config
 
 pytestmark = pytest.mark.gpu
@@ -104,7 +105,7 @@ def test_backward_full_size_crop():
         pytest.skip("no CUDA device")
     from paper_2512_11800_gb300 import Rasterizer
     R = Rasterizer()
-    sc, cam = scenes.workload("shells1M_1080p")
+    sc, cam = helpers.workload("shells1M_1080p")
     x0, y0, s = 944, 524, 32
     rng = np.random.default_rng(2)
     g_img = np.zeros((cam.height, cam.width, 3))
@@ -170,14 +171,14 @@ def test_finite_differences_on_256_gaussians():
         pytest.skip("no CUDA device")
     from paper_2512_11800_gb300 import Rasterizer
     R = Rasterizer()
-    sc, cam = scenes.workload("shells1M_1080p")
+    sc, cam = helpers.workload("shells1M_1080p")
     x0, y0, s = 956, 536, 8
     rng = np.random.default_rng(7)
     g_img = np.zeros((cam.height, cam.width, 3))
     g_img[y0:y0 + s, x0:x0 + s] = rng.normal(size=(s, s, 3))
     gg = gpu_grads(R, sc, cam, g_img, np.zeros((cam.height, cam.width)))
     cfg = oracle_config()
-    rect = O.preprocess(sc, cam, cfg).rect.numpy()
+    rect = helpers.oracle_pre("shells1M_1080p", cfg).rect.numpy()
     touch = np.where((rect[:, 0] <= x0 + s - 1) & (rect[:, 2] >= x0) & (rect[:, 1] <= y0 + s - 1) &
                      (rect[:, 3] >= y0))[0]
     sub = sc.subset(touch)

@@ -14,6 +14,7 @@ import torch
 
 import oracle as O
 import scenes
+import helpers
 from helpers import oracle_config
 
 pytestmark = pytest.mark.gpu
@@ -196,23 +197,20 @@ def test_multiview_concatenation_matches_single_views(R):
     assert torch.equal(both["T"][n0:], two["T"])
 
 
-def _crops(cam, seed, n=3, size=64):
-    rng = np.random.default_rng(seed)
-    out = [((cam.width - size) // 2, (cam.height - size) // 2, size, size)]
-    for _ in range(n):
-        out.append((int(rng.integers(0, cam.width - size)), int(rng.integers(0, cam.height - size)), size, size))
-    return out
+# crops checked on the full-size frames; the 1M crops are shared with the
+# moment-storage precision test (one oracle render per crop and session)
+FULL_SIZE_CROPS = {"clusters200k_720p": (7, 1, 64), "shells1M_1080p": (7, 2, 64)}
 
 
-@pytest.mark.parametrize("name,ncrops", [("clusters200k_720p", 2), ("shells1M_1080p", 3)])
-def test_full_size_workloads_on_crops(R, name, ncrops):
+@pytest.mark.parametrize("name", ["clusters200k_720p", "shells1M_1080p"])
+def test_full_size_workloads_on_crops(R, name):
     """Full-resolution render (the benchmark's launch configuration) checked
     against the oracle on 64x64 crops (centre + seeded)."""
-    sc, cam = scenes.workload(name)
+    sc, cam = helpers.workload(name)
     out = R.render(G(sc), cam)
     assert R.status()[0] == 0
-    for region in _crops(cam, 7, ncrops):
-        ref = O.render(sc, cam, oracle_config(), region=region)
+    for region in helpers.crops(cam, *FULL_SIZE_CROPS[name]):
+        ref = helpers.oracle_crop(name, region)
         err = compare(out, ref, cam, region)
         print(name, region, "pairs", ref["n_pairs"], "max errors", err)
         assert_parity(err)
@@ -252,6 +250,6 @@ def test_camera_inside_the_cloud(R):
 
 
 def test_full_size_outputs_are_finite(R):
-    sc, cam = scenes.workload("shells1M_1080p")
+    sc, cam = helpers.workload("shells1M_1080p")
     out = R.render(G(sc), cam)
     assert torch.isfinite(out["rgb"]).all() and torch.isfinite(out["T"]).all() and torch.isfinite(out["penalty"]).all()
