@@ -63,6 +63,8 @@ class OracleConfig:
     m_min: float = 1.0e-7       # below this total optical depth the pixel is treated as empty
     r_mult: float = 3.0         # culling sphere radius in units of max scale
     bg: tuple = (0.0, 0.0, 0.0)
+    basis: str = "power"        # "power" (Eq. 10-12) or "trig" (Eq. 13-14)
+    trig_theta: float = 0.5 * math.pi   # wrapping angle theta of the trigonometric moments (reading)
 
 
 # ----------------------------------------------------------------------------
@@ -309,6 +311,121 @@ def optical_depth(m, eta, cfg: OracleConfig):
 
 
 # ----------------------------------------------------------------------------
+# Eq. 13-14: trigonometric moments (App. C "Trigonometric Moments")
+# ----------------------------------------------------------------------------
+def erfc_first_order(a, b):
+    """1 - erf(a + i b) with erf to first order in b around the real axis
+    (App. C: erf(a + i b) ~ erf(a) + i b (2 / sqrt(pi)) e^{-a^2}); the real
+    part is written erfc(a), which keeps its digits for large a."""
+    return torch.complex(torch.special.erfc(a), -b * (2.0 / math.sqrt(math.pi)) * torch.exp(-a * a))
+
+
+def trig_gaussian_moments(mu, Sigma, w_hat, cfg: OracleConfig, erfc_fn=None):
+    """(m-tilde_k)_i, k = 0..n, of one 1D Gaussian on [t_n, inf): the integral
+    of e^{i k (2 pi - theta) g-hat(t)} w-hat e^{-(t-mu)^2/(2 Sigma^2)} with g-hat
+    linearised as u_t = a + s (t - mu) (Eq. 14, t_f -> inf):
+      w-hat sqrt(pi/2) Sigma e^{i alpha a - Sigma^2 beta^2 / 2} (1 - erf(v_n)),
+      alpha = k (2 pi - theta),  beta = alpha s,
+      v_n = (t_n - mu)/(sqrt2 Sigma) - i Sigma beta / sqrt2,
+    with erf of the complex argument to first order in its imaginary part
+    (``erfc_fn(re, im)`` = 1 - erf(re + i im); default erfc_first_order, the
+    method's).  As for the
+    power moments, the warp is linearised at c = max(mu, t_n) (reading), and
+    k = 0 is the exact total optical depth.  Returns complex (..., n+1)."""
+    erfc_fn = erfc_fn or erfc_first_order
+    tn = cfg.t_near
+    c = torch.clamp(mu, min=tn)
+    gc, dg = warp(c, cfg)
+    a = gc + dg * (mu - c)
+    k = torch.arange(cfg.n + 1, dtype=DT)
+    alpha = k * (2.0 * math.pi - cfg.trig_theta)
+    beta = alpha * dg[..., None]
+    re = ((tn - mu) / (math.sqrt(2.0) * Sigma))[..., None].expand(beta.shape)
+    im = -Sigma[..., None] * beta / math.sqrt(2.0)
+    one_minus_erf = erfc_fn(re, im)
+    mag = (w_hat * math.sqrt(math.pi / 2.0) * Sigma)[..., None] * torch.exp(-0.5 * (Sigma[..., None] * beta) ** 2)
+    phase = alpha * a[..., None]
+    return torch.polar(mag, phase) * one_minus_erf
+
+
+def trig_biased_moments(m, cfg: OracleConfig):
+    """Normalise by m0 and bias towards the moments of the uniform distribution
+    on the angles [0, 2 pi - theta] that the depths map to (reading):
+    c = (1 - alpha) m/m0 + alpha c*,  c*_k = (e^{i k A} - 1)/(i k A), A = 2 pi - theta."""
+    A = 2.0 * math.pi - cfg.trig_theta
+    k = torch.arange(1, cfg.n + 1, dtype=DT)
+    cstar = torch.cat([torch.ones(1, dtype=torch.complex128), (torch.exp(1j * k * A) - 1.0) / (1j * k * A)])
+    return (1.0 - cfg.bias_alpha) * m / m[..., :1] + cfg.bias_alpha * cstar
+
+
+def toeplitz_gram(c, n):
+    """Gram matrix G_jl = <z^j, z^l> = int conj(z)^j z^l d(measure) = c_{l-j} of
+    the monomials on the unit circle (c_{-k} = conj(c_k))."""
+    idx = torch.arange(n + 1)
+    d = idx[None, :] - idx[:, None]
+    full = torch.cat([torch.conj(c[..., 1:].flip(-1)), c], -1)          # c_{-n} .. c_n
+    return full[..., d + n]
+
+
+def trig_canonical_representation(c, phi, n):
+    """Canonical representation on the unit circle of the moments c_0..c_n
+    with a node at z_0 = e^{i phi} (Gauss-Szego rule through z_0): the other
+    nodes are the n roots of the kernel polynomial K(z, z_0) = v(z)^T G^-1
+    conj(v(z_0)), which lie on the unit circle, and the weights are
+    1 / K(z_i, z_i) (Christoffel function).  Returns (z[..., n+1], w[..., n+1])."""
+    G = toeplitz_gram(c, n)
+    powers = torch.arange(n + 1, dtype=DT)
+    z0 = torch.polar(torch.ones_like(phi), phi)
+    v0 = z0[..., None] ** powers
+    a = torch.linalg.solve(G, torch.conj(v0)[..., None])[..., 0]      # K(z, z0) = sum_j a_j z^j
+    comp = torch.zeros(a.shape[:-1] + (n, n), dtype=a.dtype)
+    comp[..., 1:, :-1] = torch.eye(n - 1, dtype=a.dtype)
+    comp[..., :, -1] = -a[..., :n] / a[..., n:n + 1]
+    r = torch.linalg.eigvals(comp)
+    for _ in range(3):                                                  # Newton polish in FP64
+        p = torch.zeros_like(r) + a[..., n:n + 1]
+        dp = torch.zeros_like(r)
+        for k in range(n - 1, -1, -1):
+            dp = dp * r + p
+            p = p * r + a[..., k:k + 1]
+        r = r - p / dp
+    z = torch.cat([z0[..., None], r], -1)
+    V = z[..., :, None] ** powers                                       # (..., n+1 nodes, n+1)
+    sol = torch.linalg.solve(G[..., None, :, :], torch.conj(V)[..., None])[..., 0]
+    K = (V * sol).sum(-1).real
+    return z, 1.0 / K
+
+
+def trig_moment_bounds(c, phi, cfg: OracleConfig):
+    """Bounds of the normalised measure of the angles [cut, phi): with angles
+    measured from the cut psi_c = 2 pi - theta/2 in the middle of the empty
+    wrapping zone (reading), L = sum of the weights of the other nodes before
+    phi, U = L + the weight of the node at phi."""
+    z, w = trig_canonical_representation(c, phi, cfg.n)
+    cut = 2.0 * math.pi - 0.5 * cfg.trig_theta
+    ang = torch.remainder(torch.angle(z) - cut, 2.0 * math.pi)
+    before = (ang[..., 1:] < ang[..., :1]).to(DT)
+    L = (w[..., 1:] * before).sum(-1)
+    return L, L + w[..., 0]
+
+
+def trig_optical_depth(m, eta, cfg: OracleConfig):
+    """tau(eta) = m0 ((1 - beta) L + beta U) from the trigonometric moments at
+    the angle phi = (2 pi - theta) eta; tau = 0 where m0 < m_min.
+    m: (..., n+1) complex moments, eta: (..., Q) warped depths."""
+    m0 = m[..., 0].real
+    empty = m0 < cfg.m_min
+    safe = torch.where(empty[..., None], torch.ones_like(m), m)
+    c = trig_biased_moments(safe, cfg)
+    cq = c[..., None, :].expand(eta.shape + (c.shape[-1],))
+    phi = (2.0 * math.pi - cfg.trig_theta) * eta
+    L, U = trig_moment_bounds(cq.reshape(-1, c.shape[-1]), phi.reshape(-1), cfg)
+    frac = ((1.0 - cfg.beta) * L + cfg.beta * U).reshape(eta.shape)
+    tau = m0[..., None] * frac
+    return torch.where(empty[..., None].expand(eta.shape), torch.zeros_like(tau), tau)
+
+
+# ----------------------------------------------------------------------------
 # Eq. 7 quadrature with the App. B sample spacing, penalty (App. D)
 # ----------------------------------------------------------------------------
 def sample_nodes(N):
@@ -495,15 +612,22 @@ def render(scene, cam, cfg: OracleConfig = None, region=None, params=None, probe
     d_g = torch.einsum("pji,pj->pi", Rg, d) / s
     Sigma, mu, w_hat = gaussian_1d(o_g, d_g, pre.w[g])
 
-    mk = gaussian_moments(mu, Sigma, w_hat, cfg)                   # (n_pairs, 2n+1)
-    m = torch.zeros(npix, 2 * cfg.n + 1, dtype=DT).index_add(0, pix, mk)
+    trig = cfg.basis == "trig"
+    if trig:
+        mk = trig_gaussian_moments(mu, Sigma, w_hat, cfg)           # (n_pairs, n+1) complex
+        m = torch.zeros(npix, cfg.n + 1, dtype=torch.complex128).index_add(0, pix, mk)
+        depth = trig_optical_depth
+    else:
+        mk = gaussian_moments(mu, Sigma, w_hat, cfg)               # (n_pairs, 2n+1)
+        m = torch.zeros(npix, 2 * cfg.n + 1, dtype=DT).index_add(0, pix, mk)
+        depth = optical_depth
 
     t = sample_points(mu, Sigma, cfg)                              # (n_pairs, N+1)
     if tau_fn is None:
         eta, _ = warp(t, cfg)
         taus = []
         for a in range(0, t.shape[0], chunk):
-            taus.append(optical_depth(m[pix[a:a + chunk]], eta[a:a + chunk], cfg))
+            taus.append(depth(m[pix[a:a + chunk]], eta[a:a + chunk], cfg))
         tau = torch.cat(taus, 0) if taus else torch.zeros_like(t)
     else:
         tau = tau_fn(pix, t)
@@ -513,7 +637,7 @@ def render(scene, cam, cfg: OracleConfig = None, region=None, params=None, probe
     O = torch.zeros(npix, dtype=DT).index_add(0, pix, O_i)
     S = torch.zeros(npix, 3, dtype=DT).index_add(0, pix, L_i)
     P = torch.zeros(npix, dtype=DT).index_add(0, pix, P_i)
-    m0 = m[:, 0]
+    m0 = m[:, 0].real
     Tf = torch.exp(-m0)
     bg = torch.tensor(cfg.bg, dtype=DT)
     rgb = ((1.0 - Tf) / torch.clamp(O, min=cfg.eps))[:, None] * S + Tf[:, None] * bg   # Eq. 15
@@ -522,7 +646,7 @@ def render(scene, cam, cfg: OracleConfig = None, region=None, params=None, probe
                n_pairs=int(g.shape[0]), pre=pre)
     if probes is not None:
         q = torch.as_tensor(probes, dtype=DT)
-        out["tau_probe"] = optical_depth(m, q.expand(npix, -1), cfg).reshape(h, w, -1)
+        out["tau_probe"] = depth(m, q.expand(npix, -1), cfg).reshape(h, w, -1)
     out["pairs"] = (g, px, py)
     return out
 
