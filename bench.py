@@ -40,29 +40,44 @@ import scenes  # noqa: E402
 
 WORKLOAD = "shells1M_1080p"
 METRIC = "Mpixel/s fwd and fwd+bwd, 1M Gaussians @1080p; fraction of roofline; err vs FP64"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+# Algorithmic work per unit of each per-pair kernel: the operations the
+# method itself needs, counted from its formulas (not this build's executed
+# instructions).  FP32 flops (an FMA counts 2) and MUFU special-function
+# operations.  Unit: the (pixel, Gaussian) pair with the pixel centre inside
+# the Gaussian's proxy rectangle.
+#   quadrature pass, N intervals (N+1 samples):
+#     40 flop + 4 MUFU per pair: the ray-parameterised 1D Gaussian (Eq. 4-6:
+#       d_g, o_g.d_g, |d_g|^2, Sigma, mu, w-hat) and the colour sums;
+#     250 flop + 12 MUFU per sample: the depth warp (10), the bound query of
+#       Eq. 8 -- orthogonal-polynomial values and kernel coefficients at eta
+#       (30), the Christoffel weight of eta (10), two roots of the degree-4
+#       kernel polynomial by four Laguerre steps each (160) and their weights
+#       (30) -- and the interval's quadrature and penalty terms (Eq. 7,
+#       App. D; 10);
+#   moment pass: 70 flop + 6 MUFU per pair (Eq. 4-6 and the nine-moment
+#     recurrence of Eq. 10-12);
+#   adjoint passes: twice their forward counterparts (reverse mode costs at
+#     least the forward arithmetic again).
+def alg_ops(kernel, n_intervals):
+    """(FP32 flops, MUFU ops) per pixel pair of the method's work."""
+    q = n_intervals + 1
+    shade = (40 + 250 * q, 4 + 12 * q)
+    moments = (70, 6)
+    return {"k_shade": shade, "k_bwd_quadrature": (2 * shade[0], 2 * shade[1]),
+            "k_moments": moments, "k_bwd_moments": (2 * moments[0], 2 * moments[1])}[kernel]
 
-# Executed FP32 work per (pixel, Gaussian) pair (FADD + FMUL + 2 FFMA, from
-# ncu's per-opcode thread instruction counts of each kernel on the 200k/720p
-# workload divided by its pixel pairs).  The ALU roofline of a kernel is
-# this work over its time against the FP32 peak.
-FP32_FLOPS_PER_PAIR = {
-    "k_shade": 1160.3,               # k_shade<3, save>: keeps the bound queries
-    "k_bwd_quadrature": 1201.4,      # k_bwd_quadrature<3, saved>
+
+# Executed work of the current kernels from one ncu capture each on the
+# 200k/720p workload (per pixel pair): FP32 flops = FADD + FMUL + 2 FFMA
+# thread instructions, all thread instructions, and DRAM bytes (read +
+# write; the saved bound queries dominate).  Scaled to a launch by its pairs.
+EXECUTED_PER_PAIR = {
+    "k_shade": dict(flops=1160.3, thread_inst=1764.4, dram_bytes=71.6),
+    "k_bwd_quadrature": dict(flops=1201.4, thread_inst=1602.7, dram_bytes=70.6),
 }
-# DRAM bytes (read + write) per pair of the same captures: the saved bound
-# queries (64 B a pair) dominate; scaled to a launch by its pixel pairs.
-DRAM_BYTES_PER_PAIR = {
-    "k_shade": 71.6,
-    "k_bwd_quadrature": 70.6,
-}
-# Thread instructions per pair from the same captures (issue-rate view:
-# peak = SMs x 4 schedulers x 32 lanes x clock).
-THREAD_INST_PER_PAIR = {
-    "k_shade": 1764.4,
-    "k_bwd_quadrature": 1602.7,
-}
+# MUFU (XU) pipe utilisation of the same captures (ncu sm__inst_executed_pipe_xu
+# as a fraction of its peak), or None before it was captured.
+XU_PIPE_FRAC = {"k_shade": None, "k_bwd_quadrature": None}
 
 
 def measured_peaks():
@@ -198,22 +213,46 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def roofline(kernel, ms, pairs, sm_max, captured=True):
-    """captured=False: the launch is a variant without a capture of its own
-    (k_shade keeping no queries): flops and instructions are those of the
-    captured variant (it adds ~10 instructions a pair to store a query), and
-    traffic is null."""
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the max SM clock
-    achieved = FP32_FLOPS_PER_PAIR[kernel] * pairs / (ms * 1e-3) / 1e12
-    issue_peak = SM_COUNT * 4 * 32 * sm_max * 1e6                          # thread instructions / s
-    issue = THREAD_INST_PER_PAIR[kernel] * pairs / (ms * 1e-3)
-    return dict(kernel=kernel, bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                traffic=DRAM_BYTES_PER_PAIR[kernel] * pairs if captured else None, flops_per_pair=FP32_FLOPS_PER_PAIR[kernel],
-                issue_frac=issue / issue_peak,
-                peak_note="FP32: %d SMs x %d lanes x 2 flop x %.0f MHz (max SM clock); executed FP32 flops per pixel "
-                          "pair from ncu opcode counts; issue_frac = thread instructions per pair x pairs / time over "
-                          "%d SMs x 4 schedulers x 32 lanes x clock; traffic = ncu DRAM bytes per pair on the "
-                          "200k/720p workload x pairs" % (SM_COUNT, FP32_LANES_PER_SM, sm_max, SM_COUNT))
+def probe_peaks(dev):
+    """Measured FP32 FMA and MUFU throughput of this GPU (library probe)."""
+    from paper_2512_11800_gb300 import _binding as B
+    lib = B.load()
+    pk = B.AluPeaks()
+    B.check(lib.mb3dgs_probe_alu_peaks(C.byref(pk), C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)),
+            "probe_alu_peaks")
+    return dict(fp32_tflops=pk.fp32_tflops, ex2_tops=pk.ex2_tops, rsqrt_tops=pk.rsqrt_tops, rcp_tops=pk.rcp_tops,
+                sin_tops=pk.sin_tops, sm_count=pk.sm_count)
+
+
+def roofline(kernel, ms, pairs, n_intervals, peaks, sm_mhz, captured=True):
+    """ALU roofline of one per-pair kernel from its CUDA-event time.
+    frac = algorithmic FP32 flops / time over the measured FP32 peak;
+    frac_xu = algorithmic MUFU ops / time over the measured MUFU rate of the
+    slower non-exponential kinds (rsqrt, rcp); issue_frac = executed thread
+    instructions (ncu) / time over SMs x 4 schedulers x 32 lanes x the SM
+    clock sampled during the timed steps.  captured=False: the launch is a
+    variant without an ncu capture of its own (k_shade keeping no queries),
+    so traffic is null."""
+    flops, mufu = alg_ops(kernel, n_intervals)
+    ex = EXECUTED_PER_PAIR[kernel]
+    sec = ms * 1e-3
+    achieved = flops * pairs / sec / 1e12
+    mufu_peak = min(peaks["rsqrt_tops"], peaks["rcp_tops"])
+    issue_peak = peaks["sm_count"] * 4 * 32 * sm_mhz * 1e6
+    return dict(kernel=kernel, bound="alu", achieved=achieved, peak=peaks["fp32_tflops"], unit="TFLOP/s",
+                frac=achieved / peaks["fp32_tflops"],
+                traffic=ex["dram_bytes"] * pairs if captured else None,
+                frac_fp32_algorithmic=achieved / peaks["fp32_tflops"],
+                frac_xu=mufu * pairs / sec / 1e12 / mufu_peak,
+                issue_frac=ex["thread_inst"] * pairs / sec / issue_peak,
+                frac_fp32_executed=ex["flops"] * pairs / sec / 1e12 / peaks["fp32_tflops"],
+                xu_pipe_frac_ncu=XU_PIPE_FRAC[kernel],
+                alg_flops_per_pair=flops, alg_mufu_per_pair=mufu, sm_count=peaks["sm_count"],
+                peak_note="peak = measured FP32 FMA throughput of this GPU (library probe, 2 flop per FFMA); "
+                          "achieved = the method's FP32 flops per pixel pair (op model in bench.py) x pairs / "
+                          "kernel time; frac_xu against the measured rsqrt/rcp MUFU rate; issue_frac and "
+                          "frac_fp32_executed from ncu per-pair counts of the kernel on the 200k/720p "
+                          "workload; traffic = ncu DRAM bytes per pair x pairs")
 
 
 class Frame:
@@ -265,7 +304,8 @@ class Frame:
             # L2 loss against the target image (the loss itself is the caller's)
             torch.sub(self.rgb, self.target, out=self.dl).mul_(2.0 / self.rgb.numel())
             B.check(lib.mb3dgs_backward_quadrature(cfg, self.arr, self.nv, P, cap, wsp, wsn,
-                                                   C.c_void_p(self.dl.data_ptr()), None, s), "backward_quadrature")
+                                                   C.c_void_p(self.dl.data_ptr()), None, None, s),
+                    "backward_quadrature")
             rec(5)
             B.check(lib.mb3dgs_backward_moments(cfg, self.arr, self.nv, P, cap, wsp, wsn, s), "backward_moments")
             rec(6)
@@ -302,6 +342,7 @@ def run_single(args, dist, rank, world, dev):
     for _ in range(args.warmup):
         fr.step(stream, with_bwd)
     torch.cuda.synchronize()
+    peaks = probe_peaks(dev)
     clocks = ClockSampler()
     if dist:
         dist.barrier()
@@ -358,7 +399,8 @@ def run_single(args, dist, rank, world, dev):
     if rank != 0:
         return None
 
-    sm_max = measured_peaks().get("sm_max_mhz", 2070.0)
+    sm_mhz = clk.get("sm_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    n_int = R.config.n_intervals
     fwd_ms = sum(stage_ms[k] for k in STAGES[:4])
     dominant = "k_bwd_quadrature" if with_bwd and stage_ms["bwd_quadrature"] > stage_ms["shade"] else "k_shade"
     dom_ms = stage_ms["bwd_quadrature" if dominant == "k_bwd_quadrature" else "shade"]
@@ -381,8 +423,9 @@ def run_single(args, dist, rank, world, dev):
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         stage_ms=stage_ms,
         pairs=pairs, tile_pairs=tile_pairs, status=st,
-        roofline=roofline(dominant, dom_ms, pairs, sm_max, captured=fr.qcap > 0),
-        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, sm_max, captured=fr.qcap > 0),
+        roofline=roofline(dominant, dom_ms, pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0),
+        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0),
+        alu_peaks=peaks,
         e2e=dict(value=world * npix / (e2e_ms * 1e-3) / 1e6, unit="Mpixel/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
         gpu_launches=int(launches),

@@ -197,11 +197,14 @@ int mb3dgs_render(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3
  * reducing per-Gaussian gradients over covered pixels, then the chain rule
  * through the preprocessing to the Gaussian parameters.  Requires the
  * workspace of the matching mb3dgs_render call (same cfg, g, cams).
- * d_dL_drgb [pixel][3]; d_dL_dpenalty [pixel] or NULL.  The proxy rectangles
+ * d_dL_drgb [pixel][3]; d_dL_dpenalty [pixel] or NULL; d_dL_dT [pixel] or NULL:
+ * the gradient with respect to the final transmittance T_final = e^{-m0}
+ * (it reaches the Gaussians through m0, dT_final/dm0 = -T_final).  The proxy rectangles
  * and culling are treated as constants. */
 int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
                     int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
-                    const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream);
+                    const float* d_dL_dpenalty, const float* d_dL_dT, const mb3dgs_gaussian_grads* grads,
+                    mb3dgs_stream_t stream);
 
 /* The three stages of mb3dgs_backward, for callers that time or interleave
  * them (same requirements as mb3dgs_backward; call them in this order).
@@ -216,7 +219,7 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
  *   (every entry of *grads is written). */
 int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                                int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
-                               const float* d_dL_dpenalty, mb3dgs_stream_t stream);
+                               const float* d_dL_dpenalty, const float* d_dL_dT, mb3dgs_stream_t stream);
 int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                             int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream);
 int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
@@ -288,6 +291,22 @@ int mb3dgs_debug_tile_lists(const mb3dgs_config* cfg, const mb3dgs_camera* cams,
 /* Total number of CUDA kernels this library has launched in the process
  * (host counter; used to report launches per step). */
 int64_t mb3dgs_launch_count(void);
+
+/* Measured ALU throughput of the current device (the denominators of the
+ * ALU roofline of the per-pair kernels; not part of the method).  fp32_tflops:
+ * FP32 FMA pipe, 2 flop per FFMA; *_tops: MUFU (XU) pipe operations per
+ * second, 1e12 units, per instruction kind. */
+typedef struct mb3dgs_alu_peaks {
+    double fp32_tflops;
+    double ex2_tops, rsqrt_tops, rcp_tops, sin_tops;
+    int sm_count;
+} mb3dgs_alu_peaks;
+
+/* Runs the throughput probes (independent FFMA / MUFU chains on every SM,
+ * several waves of full CTAs, best of three CUDA-event-timed launches each)
+ * on the stream and fills *out.  Synchronises the stream; takes ~50 ms;
+ * allocates no device memory. */
+int mb3dgs_probe_alu_peaks(mb3dgs_alu_peaks* out, mb3dgs_stream_t stream);
 
 /* Number of tiles (cfg->tile_w x cfg->tile_h pixels) over all views (host only). */
 int64_t mb3dgs_num_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views);

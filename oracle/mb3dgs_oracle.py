@@ -700,10 +700,10 @@ def exact_optical_depth(mu, Sigma, w_hat, t, cfg: OracleConfig):
 # ----------------------------------------------------------------------------
 # oracle gradient: autograd through render (roots differentiated implicitly)
 # ----------------------------------------------------------------------------
-def render_grad(scene, cam, cfg: OracleConfig = None, dL_drgb=None, dL_dP=None, region=None):
-    """Gradient of sum(dL_drgb * rgb) + sum(dL_dP * P) over the region with
-    respect to (means, scales, quats, weights, sh); proxy rectangles and
-    culling are constants (computed without gradient)."""
+def render_grad(scene, cam, cfg: OracleConfig = None, dL_drgb=None, dL_dP=None, region=None, dL_dT=None):
+    """Gradient of sum(dL_drgb * rgb) + sum(dL_dP * P) + sum(dL_dT * T) over
+    the region with respect to (means, scales, quats, weights, sh); proxy
+    rectangles and culling are constants (computed without gradient)."""
     cfg = cfg or OracleConfig()
     params = [torch.tensor(np.asarray(a, dtype=np.float64), requires_grad=True)
               for a in (scene.means, scene.scales, scene.quats, scene.weights, scene.sh)]
@@ -711,6 +711,8 @@ def render_grad(scene, cam, cfg: OracleConfig = None, dL_drgb=None, dL_dP=None, 
     loss = (out["rgb"] * torch.as_tensor(np.asarray(dL_drgb), dtype=DT)).sum()
     if dL_dP is not None:
         loss = loss + (out["P"] * torch.as_tensor(np.asarray(dL_dP), dtype=DT)).sum()
+    if dL_dT is not None:
+        loss = loss + (out["T"] * torch.as_tensor(np.asarray(dL_dT), dtype=DT)).sum()
     grads = torch.autograd.grad(loss, params, allow_unused=True)
     names = ["means", "scales", "quats", "weights", "sh"]
     res = {n: (g.detach().numpy() if g is not None else np.zeros(p.shape)) for n, g, p in zip(names, grads, params)}

@@ -124,6 +124,7 @@ class Rasterizer:
         self.device = torch.device(device)
         self._ws = None
         self._last_qcap = 0
+        self.generation = 0   # renders so far: the workspace holds the last one's state
 
     # ------------------------------------------------------------ plumbing
     def cameras(self, cams):
@@ -167,6 +168,7 @@ class Rasterizer:
         ws = self.workspace(self.workspace_bytes(cams, g.P, 0))
         gc = g.to_c()
         s = _stream(stream)
+        self.generation += 1
         B.check(self.lib.mb3dgs_preprocess(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(), 0, s),
                 "preprocess")
         B.check(self.lib.mb3dgs_bin_tiles(C.byref(self.cfg_c), arr, nv, g.P, 0, _ptr(ws), ws.numel(), s), "bin_tiles")
@@ -192,6 +194,7 @@ class Rasterizer:
             qcap = self.set_query_capacity(pp)
             need = max(need, self.workspace_bytes(cams, g.P, tp))
         ws = self.workspace(need)
+        self.generation += 1
         npix = self.num_pixels(cams)
         rgb = torch.empty(npix, 3, device=self.device)
         T = torch.empty(npix, device=self.device)
@@ -240,6 +243,7 @@ class Rasterizer:
             out = dict(rgb=torch.empty(npix, 3, device=self.device), T=torch.empty(npix, device=self.device),
                        penalty=torch.empty(npix, device=self.device) if penalty else None)
         gc = g.to_c()
+        self.generation += 1
         B.check(self.lib.mb3dgs_render(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(), int(capacity),
                                        _ptr(out["rgb"]), _ptr(out["T"]), _ptr(out.get("penalty")), _stream(stream)),
                 "render")
@@ -257,6 +261,7 @@ class Rasterizer:
             capacity = self.count_pairs(g, cams, stream)
         self.set_query_capacity(0)
         ws = self.workspace(self.workspace_bytes(cams, g.P, capacity))
+        self.generation += 1
         npix = self.num_pixels(cams)
         s = _stream(stream)
         cfg = C.byref(self.cfg_c)
@@ -291,11 +296,11 @@ class Rasterizer:
                     capacity=int(capacity))
 
     def backward(self, g: GaussianTensors, cams, capacity, dL_drgb, dL_dP=None, stream=None, grads=None,
-                 query_capacity=None):
+                 query_capacity=None, dL_dT=None):
         """Adjoint of the last ``render`` (same Gaussians, cameras, capacity and
         query capacity, by default the last render's): gradients of
-        sum(dL_drgb * rgb) + sum(dL_dP * penalty) with respect to the Gaussian
-        parameters (mb3dgs_backward)."""
+        sum(dL_drgb * rgb) + sum(dL_dP * penalty) + sum(dL_dT * T) with respect
+        to the Gaussian parameters (mb3dgs_backward)."""
         arr, nv = self.cameras(cams)
         self.set_query_capacity(self._last_qcap if query_capacity is None else query_capacity)
         ws = self._ws
@@ -308,8 +313,11 @@ class Rasterizer:
         dL_drgb = dL_drgb.contiguous().float()
         if dL_dP is not None:
             dL_dP = dL_dP.contiguous().float()
+        if dL_dT is not None:
+            dL_dT = dL_dT.contiguous().float()
         B.check(self.lib.mb3dgs_backward(C.byref(self.cfg_c), C.byref(gc), arr, nv, _ptr(ws), ws.numel(),
-                                         int(capacity), _ptr(dL_drgb), _ptr(dL_dP), C.byref(gg), _stream(stream)),
+                                         int(capacity), _ptr(dL_drgb), _ptr(dL_dP), _ptr(dL_dT), C.byref(gg),
+                                         _stream(stream)),
                 "backward")
         return grads
 
@@ -321,17 +329,23 @@ class _RenderFn(torch.autograd.Function):
                             sh.contiguous(), sh_degree)
         out = rast.render(g, cams)
         ctx.rast, ctx.cams, ctx.g, ctx.capacity, ctx.qcap = rast, cams, g, out["capacity"], out["query_capacity"]
+        ctx.generation = rast.generation
         return out["rgb"], out["T"], out["penalty"]
 
     @staticmethod
     def backward(ctx, d_rgb, d_T, d_pen):
-        # the transmittance output e^{-m0} is not differentiated (treated as a diagnostic)
-        grads = ctx.rast.backward(ctx.g, ctx.cams, ctx.capacity, d_rgb, d_pen, query_capacity=ctx.qcap)
+        if ctx.rast.generation != ctx.generation:
+            raise RuntimeError("the Rasterizer rendered again after this forward: its workspace no longer holds "
+                               "this forward's state; use one Rasterizer per pending backward")
+        if d_rgb is None:
+            d_rgb = torch.zeros(ctx.rast.num_pixels(ctx.cams), 3, device=ctx.rast.device)
+        grads = ctx.rast.backward(ctx.g, ctx.cams, ctx.capacity, d_rgb, d_pen, query_capacity=ctx.qcap, dL_dT=d_T)
         return None, None, None, grads["means"], grads["scales"], grads["quats"], grads["weights"], grads["sh"]
 
 
 def render(rast: "Rasterizer", cams, means, scales, quats, weights, sh, sh_degree):
-    """Differentiable render: returns (rgb [Npix,3], T [Npix], penalty [Npix]).
-    Backward runs the adjoint passes of mb3dgs_backward (the workspace of this
-    forward must not be reused before backward)."""
+    """Differentiable render: returns (rgb [Npix,3], T [Npix], penalty [Npix]);
+    all three are differentiable (T = e^{-m0} through the total optical depth).
+    Backward runs the adjoint passes of mb3dgs_backward; it raises if the same
+    Rasterizer rendered again in between (its workspace holds one forward)."""
     return _RenderFn.apply(rast, cams, sh_degree, means, scales, quats, weights, sh)

@@ -28,6 +28,11 @@ class Camera(C.Structure):
                 ("cy", C.c_float), ("width", C.c_int), ("height", C.c_int)]
 
 
+class AluPeaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("ex2_tops", C.c_double), ("rsqrt_tops", C.c_double),
+                ("rcp_tops", C.c_double), ("sin_tops", C.c_double), ("sm_count", C.c_int)]
+
+
 class GaussianGrads(C.Structure):
     _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("weights", C.c_void_p),
                 ("sh", C.c_void_p)]
@@ -41,7 +46,8 @@ STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace too 
 EXPORTS = ["mb3dgs_status_string", "mb3dgs_last_cuda_error", "mb3dgs_config_default", "mb3dgs_workspace_size", "mb3dgs_preprocess",
            "mb3dgs_bin_tiles", "mb3dgs_accumulate_moments", "mb3dgs_reconstruct_transmittance", "mb3dgs_shade",
            "mb3dgs_render", "mb3dgs_render_noalloc", "mb3dgs_backward", "mb3dgs_backward_quadrature",
-           "mb3dgs_backward_moments", "mb3dgs_backward_preprocess", "mb3dgs_get_status", "mb3dgs_get_pair_counts", "mb3dgs_autotune", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count"]
+           "mb3dgs_backward_moments", "mb3dgs_backward_preprocess", "mb3dgs_get_status", "mb3dgs_get_pair_counts", "mb3dgs_autotune", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count",
+           "mb3dgs_probe_alu_peaks"]
 
 _lib = None
 
@@ -62,8 +68,8 @@ def _declare(lib):
         "mb3dgs_shade": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp, vp]),
         "mb3dgs_render": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, vp, vp]),
         "mb3dgs_render_noalloc": (C.c_int, [cfg, gs, cam, C.c_int, vp, vp, vp, vp, vp]),
-        "mb3dgs_backward": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, gg, vp]),
-        "mb3dgs_backward_quadrature": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp]),
+        "mb3dgs_backward": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, vp, vp, vp, gg, vp]),
+        "mb3dgs_backward_quadrature": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp, vp]),
         "mb3dgs_backward_moments": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp]),
         "mb3dgs_backward_preprocess": (C.c_int, [cfg, gs, cam, C.c_int, vp, sz, i64, gg, vp]),
         "mb3dgs_get_status": (C.c_int, [vp, sz, P(C.c_int), P(i64), vp]),
@@ -72,6 +78,7 @@ def _declare(lib):
         "mb3dgs_debug_tile_lists": (C.c_int, [cfg, cam, C.c_int, i64, i64, vp, sz, vp, vp, vp, vp]),
         "mb3dgs_num_tiles": (i64, [cfg, cam, C.c_int]),
         "mb3dgs_launch_count": (i64, []),
+        "mb3dgs_probe_alu_peaks": (C.c_int, [P(AluPeaks), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -18,6 +18,7 @@ void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaSt
 void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t);
 void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t);
 int launch_backward_quadrature(const Params&, const ViewTable&, const Layout&, char*, const float*, const float*,
+                               const float*,
                                cudaStream_t);
 int launch_backward_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t);
 int launch_backward_preprocess(const Params&, const ViewTable&, const Layout&, char*, const mb3dgs_gaussians&,
@@ -400,12 +401,12 @@ static int check_grads(const mb3dgs_gaussians* g, const mb3dgs_gaussian_grads* g
 
 int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                                int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
-                               const float* d_dL_dpenalty, mb3dgs_stream_t stream) {
+                               const float* d_dL_dpenalty, const float* d_dL_dT, mb3dgs_stream_t stream) {
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
-    rc = launch_backward_quadrature(c.p, c.vt, c.L, static_cast<char*>(ws), d_dL_drgb, d_dL_dpenalty,
+    rc = launch_backward_quadrature(c.p, c.vt, c.L, static_cast<char*>(ws), d_dL_drgb, d_dL_dpenalty, d_dL_dT,
                                     reinterpret_cast<cudaStream_t>(stream));
     return rc ? rc : cuda_ok();
 }
@@ -434,7 +435,8 @@ int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians*
 
 int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams, int n_views,
                     void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
-                    const float* d_dL_dpenalty, const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
+                    const float* d_dL_dpenalty, const float* d_dL_dT, const mb3dgs_gaussian_grads* grads,
+                    mb3dgs_stream_t stream) {
     int rc = check_grads(g, grads);
     if (rc) return rc;
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
@@ -443,7 +445,7 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* w = static_cast<char*>(ws);
-    if ((rc = launch_backward_quadrature(c.p, c.vt, c.L, w, d_dL_drgb, d_dL_dpenalty, st))) return rc;
+    if ((rc = launch_backward_quadrature(c.p, c.vt, c.L, w, d_dL_drgb, d_dL_dpenalty, d_dL_dT, st))) return rc;
     if ((rc = launch_backward_moments(c.p, c.vt, c.L, w, st))) return rc;
     if ((rc = launch_backward_preprocess(c.p, c.vt, c.L, w, *g, *grads, st))) return rc;
     return cuda_ok();
@@ -517,7 +519,8 @@ int mb3dgs_autotune(mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_
                     if (rc == MB3DGS_OK)
                         rc = mb3dgs_render(&c, g, cams, n_views, ws, ws_bytes, cap, d_rgb, d_T_final, nullptr, stream);
                     if (rc == MB3DGS_OK && d_dL_drgb)
-                        rc = mb3dgs_backward(&c, g, cams, n_views, ws, ws_bytes, cap, d_dL_drgb, nullptr, grads, stream);
+                        rc = mb3dgs_backward(&c, g, cams, n_views, ws, ws_bytes, cap, d_dL_drgb, nullptr, nullptr, grads,
+                                             stream);
                     if (rc == MB3DGS_OK && it > 0) {
                         float ms = 0.0f;
                         if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(TPB, 2)
                      const int32_t* __restrict__ ids, const int2* __restrict__ ranges, int64_t P, int64_t npix,
                      const StatusWords* sw, const float* __restrict__ recon, const void* __restrict__ moments,
                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
-                     const float* __restrict__ dL_dP, float* __restrict__ psi_out, float* __restrict__ grec,
+                     const float* __restrict__ dL_dP, const float* __restrict__ dL_dT, float* __restrict__ psi_out,
+                     float* __restrict__ grec,
                      const int* __restrict__ pq_off, const float4* __restrict__ pq, int64_t qcap) {
     extern __shared__ float4 s_raw[];
     __shared__ int s_slot;
@@ -66,7 +67,9 @@ __global__ void __launch_bounds__(TPB, 2)
             const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
             const float O = saved[3 * npix + c.pix];
             const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
-            pa = pixel_adjoint(p, load_m0(p, moments, c.pix), S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
+            const float m0 = load_m0(p, moments, c.pix);
+            pa = pixel_adjoint(p, m0, S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
+            if (dL_dT) pa.gm0 -= expf(-m0) * dL_dT[c.pix];   // T_final = e^{-m0}
             if (SAVED) qp = pq + (size_t)pq_off[c.pix] * nq;
         }
         const int n = c.end - c.start;
@@ -338,7 +341,7 @@ __global__ void k_preprocess_bwd(Params p, ViewTable vt, const float* __restrict
 
 // Pass 1 (zeroes the record gradients first).
 int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layout& L, char* ws,
-                               const float* dL_drgb, const float* dL_dP, cudaStream_t st) {
+                               const float* dL_drgb, const float* dL_dP, const float* dL_dT, cudaStream_t st) {
     float* grec = reinterpret_cast<float*>(ws + L.grec);
     if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (L.n_tiles == 0) return MB3DGS_OK;
@@ -353,7 +356,7 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
         p, vt, t1.ts, reinterpret_cast<const float*>(ws + L.rec),
         reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
         L.npix, reinterpret_cast<const StatusWords*>(ws + L.status), reinterpret_cast<const float*>(ws + L.recon),
-        ws + L.moments, reinterpret_cast<const float*>(ws + L.saved), dL_drgb, dL_dP,
+        ws + L.moments, reinterpret_cast<const float*>(ws + L.saved), dL_drgb, dL_dP, dL_dT,
         reinterpret_cast<float*>(ws + L.dm), grec, saved_q ? reinterpret_cast<const int*>(ws + L.pq_off) : nullptr,
         saved_q ? reinterpret_cast<const float4*>(ws + L.pq) : nullptr, L.qcap);
     return MB3DGS_OK;

@@ -47,32 +47,30 @@ __global__ void __launch_bounds__(TPB) k_moments(Params p, ViewTable vt, TileSch
                                                  int64_t P, int64_t npix, StatusWords* sw,
                                                  void* __restrict__ moments, int* __restrict__ npp, int64_t qcap) {
     extern __shared__ float4 s_raw[];
-    __shared__ int s_slot;
-    float* s_rec = reinterpret_cast<float*>(s_raw);
+    float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
     if (npp && blockIdx.x == 0 && threadIdx.x == 0 && sw->n_pixpairs > (unsigned long long)qcap)
         set_status(&sw->status, MB3DGS_ERR_CAPACITY);
     const bool any = sw->n_valid != 0;
-    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
-        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
+    int fp, fx0, fy0;
+    for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
+        PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
         float acc[NMOM];
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) acc[k] = 0.0f;
-        const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         int cnt = 0;
-        for (int b = 0; b * p.batch < n; ++b) {
-            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
+        for (int pos = c.start; pos < c.end; pos += 32) {
+            const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
             if (c.inside) {
-                for (int k = 0; k < nb; ++k) {
-                    const float* r = s_rec + k * REC;
+                for (int k = 0; k < m; ++k) {
+                    const float* r = s_buf + k * REC;
                     if (!rect_contains(r, c.px, c.py)) continue;
                     const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
                     legendre_moments(p, g, acc);
                     ++cnt;
                 }
             }
-            __syncthreads();
         }
         if (c.inside) {
             if (npp) npp[c.pix] = cnt;
@@ -154,28 +152,27 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                                                float* __restrict__ saved, const int* __restrict__ pq_off,
                                                float4* __restrict__ pq, int64_t qcap) {
     extern __shared__ float4 s_raw[];
-    __shared__ int s_slot;
-    float* s_rec = reinterpret_cast<float*>(s_raw);
+    float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
     const bool any = sw->n_valid != 0;
     // saved queries: a pixel's pairs from pq_off[pix], N+1 float4 each; only
     // when the frame's pixel pairs fit (so the int32 offsets cannot overflow)
     const bool save = SAVE && sw->n_pixpairs <= (unsigned long long)qcap;
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
-    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
-        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
+    int fp, fx0, fy0;
+    for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
+        PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
         Recon R;
         if (c.inside) R = load_recon(recon, npix, c.pix);
         else R.m0 = 0.0f;
         float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, O = 0.0f, Pen = 0.0f;
-        const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         float4* qp = (save && c.inside) ? pq + (size_t)pq_off[c.pix] * nq : nullptr;
-        for (int b = 0; b * p.batch < n; ++b) {
-            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
+        for (int pos = c.start; pos < c.end; pos += 32) {
+            const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
             if (c.inside) {
-                for (int k = 0; k < nb; ++k) {
-                    const float* r = s_rec + k * REC;
+                for (int k = 0; k < m; ++k) {
+                    const float* r = s_buf + k * REC;
                     if (!rect_contains(r, c.px, c.py)) continue;
                     const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
                     const float Oi = pair_quadrature<NI, SAVE>(p, R, g, &Pen, qp);
@@ -186,14 +183,11 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                     O += Oi;
                 }
             }
-            __syncthreads();
         }
         if (c.inside) {
             // Eq. 15: L-hat = (1 - e^{-m0}) / max(eps, O) sum L_i + e^{-m0} L_bg
-            float I[NMOM];
-            load_moments(p, moments, npix, c.pix, I);
-            const float m0 = I[0];           // total optical depth, exact (Sec. 3.2)
-            const float Tf = expf(-m0);
+            const float m0 = reinterpret_cast<const float*>(moments)[c.pix];   // m0: first plane in every storage
+            const float Tf = expf(-m0);           // total optical depth m0 is exact (Sec. 3.2)
             const float scale = -expm1f(-m0) / fmaxf(p.eps, O);
             rgb[3 * c.pix + 0] = fmaf(scale, S0, Tf * p.bg[0]);
             rgb[3 * c.pix + 1] = fmaf(scale, S1, Tf * p.bg[1]);
@@ -213,7 +207,7 @@ void exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t s
 
 void launch_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
     if (L.n_tiles == 0) return;
-    const size_t smem = sizeof(float) * REC * p.batch;
+    const size_t smem = sizeof(float) * WARP_STAGE_FLOATS * WARPS;
     int* npp = L.qcap > 0 ? reinterpret_cast<int*>(ws + L.npp) : nullptr;
     const TileLaunch tl = tile_launch(p, L, ws, Q_MOMENTS, (const void*)k_moments, smem, st);
     count_launch();
@@ -241,7 +235,7 @@ void launch_reconstruct(const Params& p, const Layout& L, char* ws, const float*
 void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* ws, float* rgb, float* T_final,
                   float* penalty, cudaStream_t st) {
     if (L.n_tiles == 0) return;
-    const size_t smem = sizeof(float) * REC * p.batch;
+    const size_t smem = sizeof(float) * WARP_STAGE_FLOATS * WARPS;
     const bool save = L.qcap > 0;
     auto kern = p.n_intervals == 3 ? (save ? k_shade<3, true> : k_shade<3, false>)
               : p.n_intervals == 5 ? (save ? k_shade<5, true> : k_shade<5, false>)

@@ -91,6 +91,90 @@ TileLaunch tile_launch(const Params& p, const Layout& L, char* ws, int q, const 
 // device (outside any later stream capture); false on failure.
 bool allow_dynamic_smem(const void* func, size_t smem);
 
+// ---------------------------------------------------------------------------
+// Warp-level work of the forward passes.  A work unit is one warp footprint
+// (8 x 4 pixels) of one tile; every warp takes units on its own (no barrier
+// between the warps of a CTA), walks the tile's Gaussian list in chunks of 32,
+// keeps the records whose rectangle overlaps its footprint (ballot, order
+// kept) and stages only those into its own shared-memory buffer.  Every pixel
+// still visits its Gaussians in ascending id order, so per-pixel sums are the
+// same as with whole-tile batches.
+// ---------------------------------------------------------------------------
+constexpr int WARPS = TPB / 32;
+constexpr int WARP_STAGE_FLOATS = 32 * REC + 32;   // 32 records + their ids
+
+// Next unit of this warp: the tile (-1 when none is left) and the footprint
+// index in *fp (warp-uniform).  GRID: CTA = tile, warp w = footprint w, once.
+// QUEUE: unit u of the ordered queue is footprint u % 8 of tile order[u / 8].
+__device__ __forceinline__ int64_t next_unit(const TileSched& ts, bool first, int* fp) {
+    if (ts.order == nullptr) {
+        *fp = threadIdx.x >> 5;
+        return first ? (int64_t)blockIdx.x : -1;
+    }
+    int u = 0;
+    if ((threadIdx.x & 31) == 0) u = atomicAdd(ts.queue, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if ((int64_t)u >= ts.n_tiles * WARPS) return -1;
+    *fp = u & (WARPS - 1);
+    return (int64_t)ts.order[u / WARPS];
+}
+
+// Pixel of this lane for footprint fp of `tile`, plus the footprint's pixel
+// box [fx0, fx0 + 7] x [fy0, fy0 + 3] (for the record filter).
+__device__ __forceinline__ PixelCtx unit_ctx(const ViewTable& vt, const int2* __restrict__ ranges, int64_t P,
+                                             int64_t tile, int fp, int* fx0, int* fy0) {
+    PixelCtx c;
+    c.v = find_view(vt, tile);
+    const ViewDesc& V = vt.v[c.v];
+    const int lt = (int)(tile - V.tile_base);
+    const int tx = lt % V.tiles_x, ty = lt / V.tiles_x;
+    const int lane = threadIdx.x & 31;
+    tile_pixel(V, tx, ty, lane, fp, c.px, c.py);
+    *fx0 = c.px - (lane & 7);
+    *fy0 = c.py - (lane >> 3);
+    c.inside = c.px < V.width && c.py < V.height;
+    c.pix = V.pixel_base + (int64_t)c.py * V.width + c.px;
+    const float ux = ((float)c.px + 0.5f - V.cx) / V.fx;
+    const float uy = ((float)c.py + 0.5f - V.cy) / V.fy;
+    c.r2 = fmaf(ux, ux, fmaf(uy, uy, 1.0f));
+    c.rlen = sqrtf(c.r2);
+    const int2 rg = ranges[tile];
+    c.start = rg.x;
+    c.end = rg.y;
+    c.rec_base = (int64_t)c.v * P;
+    return c;
+}
+
+// Stage the records of list[pos, pos + 32) whose rectangle overlaps the
+// footprint box into the warp's buffer (ascending list order); returns how
+// many.  All 32 lanes call it; the buffer is ready when it returns.
+__device__ __forceinline__ int stage_warp_chunk(float* __restrict__ s_buf, const float* __restrict__ rec,
+                                                const int32_t* __restrict__ ids, int64_t rec_base, int pos, int end,
+                                                int fx0, int fy0) {
+    const int lane = threadIdx.x & 31;
+    int* s_ids = reinterpret_cast<int*>(s_buf + 32 * REC);
+    bool keep = false;
+    int id = 0;
+    if (pos + lane < end) {
+        id = ids[pos + lane];
+        const int* ri = reinterpret_cast<const int*>(rec + (rec_base + id) * REC + R_RECT);
+        const int x0 = __ldg(ri + 0), y0 = __ldg(ri + 1), x1 = __ldg(ri + 2), y1 = __ldg(ri + 3);
+        keep = x0 <= fx0 + 7 && x1 >= fx0 && y0 <= fy0 + 3 && y1 >= fy0;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    const int m = __popc(mask);
+    __syncwarp();                 // the previous chunk's records are no longer read
+    if (keep) s_ids[__popc(mask & ((1u << lane) - 1u))] = id;
+    __syncwarp();
+    for (int t = lane; t < m * (REC / 4); t += 32) {
+        const int k = t / (REC / 4), part = t % (REC / 4);
+        cp_async16(s_buf + k * REC + part * 4, rec + (rec_base + s_ids[k]) * REC + part * 4);
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    __syncwarp();
+    return m;
+}
+
 enum TileQueue { Q_MOMENTS = 0, Q_SHADE = 1, Q_BWD_QUAD = 2, Q_BWD_MOM = 3, N_QUEUES = 4 };
 
 }  // namespace mb

@@ -29,7 +29,7 @@ void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaSt
 void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t) {}
 void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t) {}
 int launch_backward_quadrature(const Params&, const ViewTable&, const Layout&, char*, const float*, const float*,
-                               cudaStream_t) { return 0; }
+                               const float*, cudaStream_t) { return 0; }
 int launch_backward_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t) { return 0; }
 int launch_backward_preprocess(const Params&, const ViewTable&, const Layout&, char*, const mb3dgs_gaussians&,
                                const mb3dgs_gaussian_grads&, cudaStream_t) { return 0; }

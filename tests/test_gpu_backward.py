@@ -3,7 +3,9 @@ against the FP64 oracle's gradient (autograd through the oracle, itself
 pinned by central finite differences in test_oracle_grad.py).
 
 Bar: relative L2 error <= 1e-3 per parameter group (means, scales, quats,
-weights, SH), proxy rectangles held fixed on both sides."""
+weights, SH) and, element by element, |GPU - oracle| <= 1e-3 max|oracle| of
+the group (so that a few wrong Gaussians cannot hide in a group norm); proxy
+rectangles held fixed on both sides."""
 import os
 
 import numpy as np
@@ -34,12 +36,13 @@ def G(sc):
     return GaussianTensors.from_scene(sc)
 
 
-def gpu_grads(R, sc, cam, g_img, gP_img):
+def gpu_grads(R, sc, cam, g_img, gP_img, gT_img=None):
     g = G(sc)
     out = R.render(g, cam)
     dr = torch.as_tensor(g_img.reshape(-1, 3), dtype=torch.float32, device="cuda")
     dp = torch.as_tensor(gP_img.reshape(-1), dtype=torch.float32, device="cuda")
-    grads = R.backward(g, cam, out["capacity"], dr, dp)
+    dT = None if gT_img is None else torch.as_tensor(gT_img.reshape(-1), dtype=torch.float32, device="cuda")
+    grads = R.backward(g, cam, out["capacity"], dr, dp, dL_dT=dT)
     torch.cuda.synchronize()
     return {k: v.detach().cpu().double().numpy().reshape(-1) for k, v in grads.items()}
 
@@ -55,7 +58,14 @@ def oracle_grad(key, *args, **kw):
 
 
 def rel_errors(gg, ref):
-    return {k: float(np.linalg.norm(gg[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
+    """Per group: relative L2 error, and the largest element error over the
+    group's largest oracle element (both held to REL by every test)."""
+    out = {}
+    for k in NAMES:
+        a, b = gg[k], ref[k].reshape(-1)
+        scale = max(float(np.abs(b).max()), 1e-30)
+        out[k] = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)), float(np.abs(a - b).max()) / scale)
+    return out
 
 
 def test_backward_uniform2k_full_image(R):
@@ -120,6 +130,33 @@ def test_backward_full_size_crop():
     assert max(err.values()) <= REL, err
 
 
+def test_transmittance_gradient(R):
+    """A loss on the final transmittance T = e^{-m0} as well: its gradient
+    reaches the Gaussians through m0 (dT/dm0 = -T)."""
+    sc = scenes.tiny_scene(P=40, seed=9, deg=3, spread=0.5)
+    cam = scenes.look_at((0.1, 0.2, -2.0), width=48, height=40, fov_deg=55)
+    rng = np.random.default_rng(3)
+    g_img = rng.normal(size=(cam.height, cam.width, 3))
+    gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
+    gT_img = rng.normal(size=(cam.height, cam.width))
+    gg = gpu_grads(R, sc, cam, g_img, gP_img, gT_img)
+    ref = oracle_grad("sh3_near_T", sc, cam, oracle_config(R.config), g_img, gP_img, dL_dT=gT_img)
+    err = rel_errors(gg, ref)
+    assert max(err.values()) <= REL, err
+
+
+def test_autograd_backward_after_another_render_raises(R):
+    from paper_2512_11800_gb300 import render
+    sc = scenes.scene_uniform(200, 18)
+    cam = scenes.look_at((0, 0, -3), width=24, height=24)
+    g = G(sc)
+    leaves = [getattr(g, k).clone().requires_grad_(True) for k in NAMES]
+    rgb, T, pen = render(R, cam, *leaves, sc.sh_degree)
+    R.render(g, cam)                      # the workspace now holds another forward
+    with pytest.raises(RuntimeError):
+        rgb.sum().backward()
+
+
 def test_autograd_function_matches_direct_call(R):
     from paper_2512_11800_gb300 import render
     sc = scenes.scene_uniform(500, 17)
@@ -128,12 +165,13 @@ def test_autograd_function_matches_direct_call(R):
     leaves = [getattr(g, k).clone().requires_grad_(True) for k in NAMES]
     rgb, T, pen = render(R, cam, *leaves, sc.sh_degree)
     target = torch.rand_like(rgb)
-    loss = ((rgb - target) ** 2).mean() + 0.1 * pen.mean()
+    loss = ((rgb - target) ** 2).mean() + 0.1 * pen.mean() + 0.2 * T.mean()
     auto = torch.autograd.grad(loss, leaves)
     dr = (2.0 * (rgb - target) / rgb.numel()).detach()
     dp = torch.full_like(pen, 0.1 / pen.numel())
+    dT = torch.full_like(T, 0.2 / T.numel())
     out = R.render(g, cam)
-    direct = R.backward(g, cam, out["capacity"], dr, dp)
+    direct = R.backward(g, cam, out["capacity"], dr, dp, dL_dT=dT)
     for k, a in zip(NAMES, auto):
         b = direct[k]
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-7), k
@@ -214,6 +252,8 @@ def test_finite_differences_on_256_gaussians():
     fd, an = np.array(errs).T
     scale = np.abs(fd).max()
     rel = np.abs(fd - an) / (np.abs(fd) + 1e-3 * scale + 1e-12)
-    print("FD on", n_ok, "Gaussians: median rel", float(np.median(rel)), "max", float(rel.max()))
+    worst = np.argsort(rel)[-5:][::-1]
+    print("FD on", n_ok, "Gaussians: median rel", float(np.median(rel)), "95th", float(np.quantile(rel, 0.95)),
+          "max", float(rel.max()), "worst (fd, gpu):", [(float(fd[i]), float(an[i])) for i in worst])
     assert n_ok >= 200
-    assert np.median(rel) < 1e-3 and np.quantile(rel, 0.95) < 2e-2
+    assert np.median(rel) < 1e-3 and np.quantile(rel, 0.95) < 5e-3
