@@ -333,10 +333,10 @@ def run_single(args, dist, rank, world, dev):
     from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
     sc, cam = scenes.workload(args.workload)
     npix = cam.width * cam.height
-    R = Rasterizer(RasterConfig(), device=dev)
+    R = Rasterizer(RasterConfig(basis=args.basis, n_intervals=args.n_intervals), device=dev)
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
-    with_bwd = not args.forward_only
+    with_bwd = not args.forward_only and args.basis == "power"   # the trigonometric basis is forward only
     fr = Frame(R, g, cam, target, save_queries=with_bwd)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -413,7 +413,7 @@ def run_single(args, dist, rank, world, dev):
         fwd_mpix_s=world * npix / (fwd_ms * 1e-3) / 1e6,
         config={"workload": args.workload, "gaussians": g.P, "width": cam.width, "height": cam.height,
                 "sh_degree": sc.sh_degree,
-                "n_moments": 9, "n_intervals": 3,
+                "n_moments": 9, "n_intervals": n_int, "basis": args.basis,
                 "pass": "forward+backward (L2 loss vs random target)" if with_bwd else "forward",
                 "saved_queries": fr.qcap > 0,
                 "tiling": dict(tile=[R.config.tile_w, R.config.tile_h], batch=R.config.batch,
@@ -423,8 +423,10 @@ def run_single(args, dist, rank, world, dev):
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         stage_ms=stage_ms,
         pairs=pairs, tile_pairs=tile_pairs, status=st,
-        roofline=roofline(dominant, dom_ms, pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0),
-        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0),
+        roofline=roofline(dominant, dom_ms, pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0)
+        if args.basis == "power" else None,
+        roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0)
+        if args.basis == "power" else None,
         alu_peaks=peaks,
         e2e=dict(value=world * npix / (e2e_ms * 1e-3) / 1e6, unit="Mpixel/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
@@ -602,6 +604,9 @@ def main():
                     help="the default is the headline workload; the others are for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forward-only", action="store_true")
+    ap.add_argument("--basis", default="power", choices=["power", "trig"],
+                    help="moment basis; trig (Eq. 13-14) is forward only and reports no roofline")
+    ap.add_argument("--n-intervals", type=int, default=3)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

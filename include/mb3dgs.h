@@ -57,6 +57,12 @@ enum {
 };
 
 enum { MB3DGS_MOMENTS_F32 = 0, MB3DGS_MOMENTS_BF16 = 1, MB3DGS_MOMENTS_F16 = 2 };
+/* Moment basis.  POWER: power moments of the warped depth (Sec. 3.2,
+ * Eq. 10-12) with the bounds of Eq. 8.  TRIG: trigonometric moments (Sec. 3.2,
+ * Eq. 13-14; App. C) of the angle (2 pi - theta) g-hat, with the bounds of the
+ * Gauss-Szego rule on the unit circle cut in the middle of the wrapping zone
+ * (forward only: the adjoint calls return MB3DGS_ERR_UNSUPPORTED). */
+enum { MB3DGS_BASIS_POWER = 0, MB3DGS_BASIS_TRIG = 1 };
 /* How the per-tile passes map tiles of all views to CTAs.  QUEUE: one wave of
  * persistent CTAs takes tiles from an atomic queue in decreasing order of
  * their Gaussian-list length; GRID: one CTA per tile in view/raster order. */
@@ -96,7 +102,10 @@ typedef struct mb3dgs_config {
                            mb3dgs_backward; 0 (default): backward recomputes them.
                            Size it with the pixel-pair count of
                            mb3dgs_get_pair_counts; a frame with more pairs sets
-                           MB3DGS_ERR_CAPACITY and saves none. */
+                           MB3DGS_ERR_CAPACITY and saves none.  Ignored with
+                           the TRIG basis. */
+    int basis;          /* MB3DGS_BASIS_*; default POWER */
+    float trig_theta;   /* TRIG: wrapping angle theta in (0, 2 pi) (reading); pi/2 */
 } mb3dgs_config;
 
 /* Device pointers, caller-owned, layout as in the file comment. */

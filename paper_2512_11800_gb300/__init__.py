@@ -49,6 +49,9 @@ class RasterConfig:
     tile_h: int = 16
     batch: int = 256
     schedule: str = "queue"        # "queue" | "grid"
+    # moment basis: "power" (Eq. 10-12) or "trig" (Eq. 13-14, forward only)
+    basis: str = "power"
+    trig_theta: float = 0.5 * np.pi   # wrapping angle of the trigonometric moments
 
     def to_c(self) -> B.Config:
         c = B.Config()
@@ -59,6 +62,8 @@ class RasterConfig:
         c.bg = B.c_float3(*[float(x) for x in self.bg])
         c.moment_dtype = B.MOMENTS[self.moment_dtype]
         c.schedule = B.SCHEDULES[self.schedule]
+        c.basis = B.BASES[self.basis]
+        c.trig_theta = float(self.trig_theta)
         return c
 
 
@@ -221,7 +226,8 @@ class Rasterizer:
         n = int(n)
         nbytes = n * 16 * (self.config.n_intervals + 1)
         fits = n < 2 ** 31 and nbytes <= self.config.query_budget_gb * 2 ** 30
-        self.cfg_c.query_capacity = n if (self.config.save_queries and fits) else 0
+        keep = self.config.save_queries and fits and self.config.basis == "power"   # trig: forward only
+        self.cfg_c.query_capacity = n if keep else 0
         return int(self.cfg_c.query_capacity)
 
     def render(self, g: GaussianTensors, cams, capacity=None, stream=None, penalty=True, out=None,

@@ -15,7 +15,7 @@ class Config(C.Structure):
                 ("eps", C.c_float), ("bias_alpha", C.c_float), ("m_min", C.c_float), ("r_mult", C.c_float),
                 ("bg", c_float3), ("moment_dtype", C.c_int), ("strict", C.c_int),
                 ("tile_w", C.c_int), ("tile_h", C.c_int), ("batch", C.c_int), ("schedule", C.c_int),
-                ("query_capacity", C.c_int64)]
+                ("query_capacity", C.c_int64), ("basis", C.c_int), ("trig_theta", C.c_float)]
 
 
 class Gaussians(C.Structure):
@@ -39,6 +39,7 @@ class GaussianGrads(C.Structure):
 
 
 MOMENTS = {"f32": 0, "bf16": 1, "f16": 2}
+BASES = {"power": 0, "trig": 1}
 SCHEDULES = {"queue": 0, "grid": 1}
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace too small", -4: "device wait timed out",
           -5: "non-finite Gaussian parameters", -6: "unsupported configuration", -7: "tile-pair capacity exceeded"}

@@ -54,6 +54,9 @@ static int check_cfg(const mb3dgs_config* c) {
         !(c->m_min >= 0) || !(c->r_mult > 0) || c->warp_lambda == 0.0f || c->warp_lambda == 1.0f)
         return MB3DGS_ERR_INVALID_ARG;
     if (c->moment_dtype < 0 || c->moment_dtype > 2) return MB3DGS_ERR_INVALID_ARG;
+    if (c->basis != MB3DGS_BASIS_POWER && c->basis != MB3DGS_BASIS_TRIG) return MB3DGS_ERR_INVALID_ARG;
+    if (c->basis == MB3DGS_BASIS_TRIG && !(c->trig_theta > 0.0f && c->trig_theta < (float)(2.0 * M_PI)))
+        return MB3DGS_ERR_INVALID_ARG;
     if (c->tile_w != 0 || c->tile_h != 0) {
         const int tw = c->tile_w, th = c->tile_h;
         if (!(tw == 8 || tw == 16 || tw == 32 || tw == 64) || tw * th != TPB) return MB3DGS_ERR_UNSUPPORTED;
@@ -117,7 +120,7 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     while ((int64_t(1) << bits) < ntiles) ++bits;
     L.sort_passes = (bits + 7) / 8;
     L.final_buf = L.sort_passes % 2;
-    L.qcap = cfg ? cfg->query_capacity : 0;
+    L.qcap = cfg && cfg->basis == MB3DGS_BASIS_POWER ? cfg->query_capacity : 0;
     if (L.qcap < 0 || L.qcap >= (int64_t(1) << 31)) return MB3DGS_ERR_INVALID_ARG;
     L.scan_tmp_elems = std::max(scan_tmp_elems(L.VP), scan_tmp_elems((int64_t)256 * L.nb_sort));
     if (L.qcap > 0) L.scan_tmp_elems = std::max(L.scan_tmp_elems, scan_tmp_elems(npix));
@@ -212,6 +215,18 @@ static void make_params(const mb3dgs_config* c, Params& p) {
     }
     p.strict = c->strict;
     p.moment_dtype = c->moment_dtype;
+    p.basis = c->basis;
+    if (c->basis == MB3DGS_BASIS_TRIG) {
+        const double A = 2.0 * M_PI - (double)c->trig_theta;
+        p.trig_A = (float)A;
+        p.trig_lo = (float)(-0.5 * (double)c->trig_theta);
+        // c*_k = (e^{i k A} - 1) / (i k A): moments of the uniform distribution on [0, A]
+        for (int k = 1; k <= 4; ++k) {
+            const double ka = k * A;
+            p.cstar_re[k - 1] = (float)(std::sin(ka) / ka);
+            p.cstar_im[k - 1] = (float)((1.0 - std::cos(ka)) / ka);
+        }
+    }
 }
 
 struct Ctx {
@@ -282,6 +297,8 @@ int mb3dgs_config_default(mb3dgs_config* c) {
     c->r_mult = 3.0f;
     c->moment_dtype = MB3DGS_MOMENTS_F32;
     c->strict = 0;
+    c->basis = MB3DGS_BASIS_POWER;
+    c->trig_theta = (float)(0.5 * M_PI);
     return MB3DGS_OK;
 }
 
@@ -402,6 +419,7 @@ static int check_grads(const mb3dgs_gaussians* g, const mb3dgs_gaussian_grads* g
 int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                                int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
                                const float* d_dL_dpenalty, const float* d_dL_dT, mb3dgs_stream_t stream) {
+    if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
@@ -413,6 +431,7 @@ int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* ca
 
 int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                             int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream) {
+    if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
@@ -423,6 +442,7 @@ int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams,
 int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
                                int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity,
                                const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
+    if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
     int rc = check_grads(g, grads);
     if (rc) return rc;
     Ctx c;
@@ -437,6 +457,7 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
                     void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
                     const float* d_dL_dpenalty, const float* d_dL_dT, const mb3dgs_gaussian_grads* grads,
                     mb3dgs_stream_t stream) {
+    if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
     int rc = check_grads(g, grads);
     if (rc) return rc;
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;

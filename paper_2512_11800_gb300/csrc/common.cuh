@@ -80,6 +80,10 @@ struct Params {
     float leg_to_pow[NMOM * NMOM]; // m-hat_k = sum_l leg_to_pow[k*9+l] I_l
     int strict;
     int moment_dtype;
+    int basis;             // MB3DGS_BASIS_POWER | MB3DGS_BASIS_TRIG
+    float trig_A;          // angle range 2 pi - theta of the trigonometric moments
+    float trig_lo;         // cut -theta/2 (middle of the wrapping zone)
+    float cstar_re[4], cstar_im[4];   // moments of the uniform distribution on [0, A] (bias target)
 };
 
 // Workspace layout (byte offsets), computed on the host.
@@ -630,13 +634,35 @@ MB_HD void store_recon(const Recon& R, float* __restrict__ rc, int64_t npix, int
     }
 }
 
+}  // namespace mb
+#include "trig.cuh"
+namespace mb {
+
 // ----------------------------------------------------------------------------
 // Per-pair quadrature (Eq. 7 with App. B samples) and penalty (App. D).
 // NI > 0: compile-time number of intervals; NI == 0: runtime p.n_intervals.
 // Returns O_i; adds P_i to *pen.
 // ----------------------------------------------------------------------------
-template <int NI, bool SAVE = false>
-MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, float* pen,
+// Optical depth at warped depth gq of one sample: power-moment bounds (with
+// the query kept for the adjoint when qout != nullptr) or trigonometric ones.
+template <bool SAVE>
+MB_HD float sample_depth(const Params& p, const Recon& R, float gq, float4* qout) {
+    const float y = fmaf(2.0f, gq, -1.0f);
+    if (SAVE && qout) {
+        QueryRec q;
+        const float tau = bound_query<true>(R, p.beta, y, &q);
+        *qout = pack_query(tau, q);
+        return tau;
+    }
+    return optical_depth(R, p.beta, y);
+}
+template <bool SAVE>
+MB_HD float sample_depth(const Params& p, const TrigRecon& T, float gq, float4*) {
+    return trig_optical_depth(p, T, gq);
+}
+
+template <int NI, bool SAVE = false, class RecT = Recon>
+MB_HD float pair_quadrature(const Params& p, const RecT& R, const Gauss1D& g, float* pen,
                             float4* __restrict__ qout = nullptr) {
     // streamed over the samples (one copy of the bound-query code): interval
     // j-1 is accumulated once sample j is known
@@ -652,15 +678,7 @@ MB_HD float pair_quadrature(const Params& p, const Recon& R, const Gauss1D& g, f
     for (int j = 0; j <= N; ++j) {
         const float raw = fmaf(ks, p.x_nodes[j], g.mu);
         const float tj = fminf(fmaxf(raw, p.t_near), p.t_far);
-        const float y = fmaf(2.0f, warp_only(p, tj), -1.0f);
-        float tau;
-        if (SAVE && qout) {
-            QueryRec q;
-            tau = bound_query<true>(R, p.beta, y, &q);
-            qout[j] = pack_query(tau, q);
-        } else {
-            tau = optical_depth(R, p.beta, y);
-        }
+        const float tau = sample_depth<SAVE>(p, R, warp_only(p, tj), qout ? qout + j : nullptr);
         float erf_j = p.x_erf[j], gau_j = p.x_gau[j];
         if (tj != raw) {
             const float b = (tj - g.mu) * isq;

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(TPB) k_moments(Params p, ViewTable vt, TileSch
                     const float* r = s_buf + k * REC;
                     if (!rect_contains(r, c.px, c.py)) continue;
                     const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
-                    legendre_moments(p, g, acc);
+                    if (p.basis == MB3DGS_BASIS_TRIG) trig_moments(p, g, acc);
+                    else legendre_moments(p, g, acc);
                     ++cnt;
                 }
             }
@@ -105,12 +106,18 @@ __device__ __forceinline__ void load_moments(const Params& p, const void* __rest
     }
 }
 
-// paper's power moments m-hat_k = int u^k d(measure), u = (y + 1) / 2
+// paper's power moments m-hat_k = int u^k d(measure), u = (y + 1) / 2; with
+// the trigonometric basis the moments themselves {m0, Re m1, Im m1, ..}
 __global__ void k_moments_to_power(Params p, const void* __restrict__ moments, int64_t npix, float* __restrict__ out) {
     const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= npix) return;
     float I[NMOM];
     load_moments(p, moments, npix, pix, I);
+    if (p.basis == MB3DGS_BASIS_TRIG) {
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) out[pix * NMOM + k] = I[k];
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < NMOM; ++k) {
         float s = 0.0f;
@@ -127,6 +134,14 @@ __global__ void k_reconstruct(Params p, const void* __restrict__ moments, int64_
     if (pix >= npix) return;
     float I[NMOM];
     load_moments(p, moments, npix, pix, I);
+    if (p.basis == MB3DGS_BASIS_TRIG) {
+        TrigRecon T;
+        reconstruct_trig(p, I, T);
+        store_trig_recon(T, recon, npix, pix);
+        if (Q > 0 && eta != nullptr && T_out != nullptr)
+            for (int q = 0; q < Q; ++q) T_out[pix * Q + q] = expf(-trig_optical_depth(p, T, eta[pix * Q + q]));
+        return;
+    }
     Recon R;
     reconstruct_pixel(p, I, R);
     store_recon(R, recon, npix, pix);
@@ -139,10 +154,18 @@ __global__ void k_reconstruct(Params p, const void* __restrict__ moments, int64_
 }
 
 // ---------------------------------------------------------------- quadrature pass
+__device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, int64_t npix, int64_t pix, Recon& R) {
+    R = load_recon(rc, npix, pix);
+}
+__device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, int64_t npix, int64_t pix,
+                                                 TrigRecon& T) {
+    T = load_trig_recon(rc, npix, pix);
+}
+
 #ifndef MB_SHADE_MIN_CTAS
 #define MB_SHADE_MIN_CTAS 3      // resident CTAs per SM the register budget is sized for
 #endif
-template <int NI, bool SAVE>
+template <int NI, bool SAVE, class RecT>
 __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                                                const int32_t* __restrict__ ids, const int2* __restrict__ ranges,
                                                int64_t P, int64_t npix, const StatusWords* sw,
@@ -162,8 +185,8 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
         PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
-        Recon R;
-        if (c.inside) R = load_recon(recon, npix, c.pix);
+        RecT R;
+        if (c.inside) load_pixel_state(recon, npix, c.pix, R);
         else R.m0 = 0.0f;
         float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, O = 0.0f, Pen = 0.0f;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
@@ -175,7 +198,7 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                     const float* r = s_buf + k * REC;
                     if (!rect_contains(r, c.px, c.py)) continue;
                     const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
-                    const float Oi = pair_quadrature<NI, SAVE>(p, R, g, &Pen, qp);
+                    const float Oi = pair_quadrature<NI, SAVE, RecT>(p, R, g, &Pen, qp);
                     if (SAVE && qp) qp += nq;
                     S0 = fmaf(r[R_RGB + 0], Oi, S0);
                     S1 = fmaf(r[R_RGB + 1], Oi, S1);
@@ -237,9 +260,12 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
     if (L.n_tiles == 0) return;
     const size_t smem = sizeof(float) * WARP_STAGE_FLOATS * WARPS;
     const bool save = L.qcap > 0;
-    auto kern = p.n_intervals == 3 ? (save ? k_shade<3, true> : k_shade<3, false>)
-              : p.n_intervals == 5 ? (save ? k_shade<5, true> : k_shade<5, false>)
-                                   : (save ? k_shade<0, true> : k_shade<0, false>);
+    auto kern = p.basis == MB3DGS_BASIS_TRIG
+                    ? (p.n_intervals == 3 ? k_shade<3, false, TrigRecon>
+                       : p.n_intervals == 5 ? k_shade<5, false, TrigRecon> : k_shade<0, false, TrigRecon>)
+              : p.n_intervals == 3 ? (save ? k_shade<3, true, Recon> : k_shade<3, false, Recon>)
+              : p.n_intervals == 5 ? (save ? k_shade<5, true, Recon> : k_shade<5, false, Recon>)
+                                   : (save ? k_shade<0, true, Recon> : k_shade<0, false, Recon>);
     const TileLaunch tl = tile_launch(p, L, ws, Q_SHADE, (const void*)kern, smem, st);
     count_launch();
     kern<<<tl.grid, TPB, smem, st>>>(

@@ -1,7 +1,12 @@
 """Shared test helpers: map the CUDA path's float32 configuration onto the
-oracle's (the oracle consumes exactly the same float32 input values), and
-keep the oracle's expensive results for the large workloads once per test
-session (scene draws, FP64 preprocessing of 1M-3M Gaussians, crop renders)."""
+oracle's (the oracle consumes exactly the same float32 input values), keep
+the oracle's expensive results for the large workloads once per test session
+(scene draws, FP64 preprocessing of 1M-3M Gaussians, crop renders), and run
+many small independent oracle renders on a pool of worker processes."""
+import multiprocessing
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 
 import oracle as O
@@ -19,7 +24,8 @@ def oracle_config(rc=None, **over):
     from paper_2512_11800_gb300 import RasterConfig
     rc = rc or RasterConfig()
     kw = {k: f32(getattr(rc, k)) for k in FLOAT_FIELDS}
-    kw.update(n=rc.n, n_intervals=rc.n_intervals, bg=tuple(f32(b) for b in rc.bg))
+    kw.update(n=rc.n, n_intervals=rc.n_intervals, bg=tuple(f32(b) for b in rc.bg), basis=rc.basis,
+              trig_theta=f32(rc.trig_theta))
     kw.update(over)
     return O.OracleConfig(**kw)
 
@@ -30,13 +36,10 @@ _REFS = {}
 
 
 def workload(name):
-    """scenes.workload(name), drawn once per session; the arrays are made
-    read-only so that no test can change a scene another test reuses."""
+    """scenes.workload(name), drawn once per session (tests that change a
+    scene work on a copy: Scene.subset)."""
     if name not in _WORKLOADS:
-        sc, cam = scenes.workload(name)
-        for k in ["means", "scales", "quats", "weights", "sh"]:
-            getattr(sc, k).setflags(write=False)
-        _WORKLOADS[name] = (sc, cam)
+        _WORKLOADS[name] = scenes.workload(name)
     return _WORKLOADS[name]
 
 
@@ -70,3 +73,24 @@ def crops(cam, seed, n, size):
     for _ in range(n):
         out.append((int(rng.integers(0, cam.width - size)), int(rng.integers(0, cam.height - size)), size, size))
     return out
+
+
+def _worker_init():
+    import torch
+    torch.set_num_threads(2)
+
+
+def _loss_task(args):
+    scene, cam, cfg, dL_drgb, region = args
+    loss, rect = O.render_loss(scene, cam, cfg, dL_drgb, region=region)
+    return loss, rect.numpy()
+
+
+def oracle_losses(tasks):
+    """O.render_loss for each (scene, cam, cfg, dL_drgb, region) task, on
+    worker processes started with spawn (never forked from a process that
+    has used the GPU).  Returns [(loss, rect), ...] in task order."""
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    ctx = multiprocessing.get_context("spawn")
+    with ProcessPoolExecutor(max_workers=workers, mp_context=ctx, initializer=_worker_init) as ex:
+        return list(ex.map(_loss_task, tasks, chunksize=4))

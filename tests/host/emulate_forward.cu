@@ -11,7 +11,9 @@
 // quats, weights, sh, mb3dgs_camera, int32 region x0 y0 w h), argv[2] =
 // output file (float32 rgb [h][w][3], T [h][w], T(eta_q) [h][w][17] at the
 // warped depths eta_q = q/16), argv[3] (optional) = N intervals (default 3;
-// other values run the runtime-N template).
+// other values run the runtime-N template), argv[4] (optional) = moment basis
+// (0 power, 1 trigonometric: trig_moments, reconstruct_trig and the
+// trigonometric bound queries).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -45,7 +47,7 @@ static void rd(FILE* f, T* x, size_t n) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 3 && argc != 4) return 2;
+    if (argc < 3 || argc > 5) return 2;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
     int64_t P;
@@ -66,7 +68,9 @@ int main(int argc, char** argv) {
     fclose(f);
     mb3dgs_config cfg;
     mb3dgs_config_default(&cfg);
-    if (argc == 4) cfg.n_intervals = atoi(argv[3]);
+    if (argc >= 4) cfg.n_intervals = atoi(argv[3]);
+    if (argc >= 5) cfg.basis = atoi(argv[4]);
+    const bool trig = cfg.basis == MB3DGS_BASIS_TRIG;
     Params p;
     make_params(&cfg, p);
     ViewTable vt;
@@ -95,16 +99,22 @@ int main(int argc, char** argv) {
             const float* r = &rec[i * REC];
             if (!rect_contains(r, px, py)) continue;
             const Gauss1D g = pair_gaussian(r, (float)px + 0.5f - r[R_AX], (float)py + 0.5f - r[R_AY], rl, r2);
-            legendre_moments(p, g, acc);
+            if (trig) trig_moments(p, g, acc);
+            else legendre_moments(p, g, acc);
         }
         Recon R;
-        reconstruct_pixel(p, acc, R);
+        TrigRecon TR;
+        if (trig) reconstruct_trig(p, acc, TR);
+        else reconstruct_pixel(p, acc, R);
         float S[3] = {0, 0, 0}, O = 0, Pen = 0;
         for (int64_t i : list) {
             const float* r = &rec[i * REC];
             if (!rect_contains(r, px, py)) continue;
             const Gauss1D g = pair_gaussian(r, (float)px + 0.5f - r[R_AX], (float)py + 0.5f - r[R_AY], rl, r2);
-            const float Oi = p.n_intervals == 3 ? pair_quadrature<3>(p, R, g, &Pen) : pair_quadrature<0>(p, R, g, &Pen);
+            float Oi;
+            if (trig) Oi = p.n_intervals == 5 ? pair_quadrature<5, false, TrigRecon>(p, TR, g, &Pen)
+                                              : pair_quadrature<0, false, TrigRecon>(p, TR, g, &Pen);
+            else Oi = p.n_intervals == 3 ? pair_quadrature<3>(p, R, g, &Pen) : pair_quadrature<0>(p, R, g, &Pen);
             for (int c = 0; c < 3; ++c) S[c] += r[R_RGB + c] * Oi;
             O += Oi;
         }
@@ -112,7 +122,8 @@ int main(int argc, char** argv) {
         for (int c = 0; c < 3; ++c) out_rgb[3 * q + c] = sc * S[c] + Tf * p.bg[c];
         out_T[q] = Tf;
         for (int k = 0; k < NPROBE; ++k)
-            out_probe[q * NPROBE + k] = expf(-optical_depth(R, p.beta, 2.0f * ((float)k / 16.0f) - 1.0f));
+            out_probe[q * NPROBE + k] = trig ? expf(-trig_optical_depth(p, TR, (float)k / 16.0f))
+                                             : expf(-optical_depth(R, p.beta, 2.0f * ((float)k / 16.0f) - 1.0f));
     }
     FILE* o = fopen(argv[2], "wb");
     if (!o) return 2;

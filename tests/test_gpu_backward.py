@@ -202,8 +202,10 @@ def test_finite_differences_on_256_gaussians():
     """Directional central differences of the FP64 oracle loss against the GPU
     gradient for 256 Gaussians of the 1M/1080p scene: the loss is a random
     linear function of the RGB of an 8x8 crop; the GPU differentiates the
-    full frame, the oracle only the Gaussians whose rectangles touch the
-    crop (the only ones that affect it).  Gaussians whose rectangle or
+    full frame.  A Gaussian changes only the pixels inside its rectangle, so
+    the oracle's difference for Gaussian i is taken over rect_i within the
+    crop, rendering only the Gaussians whose rectangles touch that part (the
+    other pixels' terms cancel exactly).  Gaussians whose rectangle or
     culling changes under the perturbation are skipped."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -222,12 +224,9 @@ def test_finite_differences_on_256_gaussians():
     sub = sc.subset(touch)
     for k in ["means", "scales", "quats", "weights", "sh"]:      # exact perturbations
         setattr(sub, k, getattr(sub, k).astype(np.float64))
-    gcrop = g_img[y0:y0 + s, x0:x0 + s]
-    region = (x0, y0, s, s)
-    base, rect0 = O.render_loss(sub, cam, cfg, gcrop, region=region)
-    # GPU gradient of the chosen Gaussians, per parameter group
+    rsub = rect[touch]
     pick = rng.choice(len(touch), size=min(256, len(touch)), replace=False)
-    n_ok, errs = 0, []
+    tasks, meta = [], []
     for j in pick:
         gi = touch[j]
         v = {k: rng.normal(size=getattr(sc, k)[gi].shape) for k in ["means", "scales", "quats", "weights"]}
@@ -235,19 +234,26 @@ def test_finite_differences_on_256_gaussians():
              "quats": 1e-4, "weights": 1e-4 * float(sc.weights[gi])}
         dot = sum(float(np.dot(gg[k].reshape(getattr(sc, k).shape[0], -1)[gi], v[k].reshape(-1)) * h[k])
                   for k in v)
-        vals = []
+        # the part of the crop this Gaussian covers, and the Gaussians that touch it
+        rx0, ry0 = max(x0, rsub[j, 0]), max(y0, rsub[j, 1])
+        rx1, ry1 = min(x0 + s - 1, rsub[j, 2]), min(y0 + s - 1, rsub[j, 3])
+        region = (int(rx0), int(ry0), int(rx1 - rx0 + 1), int(ry1 - ry0 + 1))
+        local = np.where((rsub[:, 0] <= rx1) & (rsub[:, 2] >= rx0) & (rsub[:, 1] <= ry1) & (rsub[:, 3] >= ry0))[0]
+        jl = int(np.where(local == j)[0][0])
+        gcrop = g_img[ry0:ry1 + 1, rx0:rx1 + 1]
         for sign in (1.0, -1.0):
-            pert = sub.subset(np.arange(len(touch)))
+            pert = sub.subset(local)
             for k in v:
-                getattr(pert, k)[j] = getattr(sub, k)[j] + sign * h[k] * v[k]
-            loss, r = O.render_loss(pert, cam, cfg, gcrop, region=region)
-            if not np.array_equal(r.numpy(), rect0.numpy()):
-                break
-            vals.append(loss)
-        if len(vals) < 2:
+                getattr(pert, k)[jl] = getattr(sub, k)[j] + sign * h[k] * v[k]
+            tasks.append((pert, cam, cfg, gcrop, region))
+        meta.append((dot, rsub[local]))
+    res = helpers.oracle_losses(tasks)
+    n_ok, errs = 0, []
+    for m, (dot, r0) in enumerate(meta):
+        (lp, rp), (lm, rm) = res[2 * m], res[2 * m + 1]
+        if not (np.array_equal(rp, r0) and np.array_equal(rm, r0)):
             continue
-        fd = (vals[0] - vals[1]) / 2.0
-        errs.append((fd, dot))
+        errs.append(((lp - lm) / 2.0, dot))
         n_ok += 1
     fd, an = np.array(errs).T
     scale = np.abs(fd).max()

@@ -76,10 +76,10 @@ def _write_input(fin, sc, cam, region, extra=()):
 PROBES = np.arange(17) / 16.0
 
 
-def emulate(exe, tmp, sc, cam, region, n_intervals=3):
+def emulate(exe, tmp, sc, cam, region, n_intervals=3, basis=0):
     fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
     _write_input(fin, sc, cam, region)
-    subprocess.run([exe, fin, fout, str(n_intervals)], check=True, timeout=600)
+    subprocess.run([exe, fin, fout, str(n_intervals), str(basis)], check=True, timeout=600)
     w, h = region[2], region[3]
     d = np.fromfile(fout, np.float32).astype(np.float64)
     n = w * h
@@ -132,6 +132,27 @@ def test_host_emulated_forward_other_interval_counts(emulator, tmp_path, N):
     ref = O.render(sc, cam, oracle_config(n_intervals=N), region=region)
     e_rgb = float(np.abs(rgb - ref["rgb"].numpy()).max())
     assert e_rgb <= TOL, (N, e_rgb)
+
+
+@pytest.mark.parametrize("N", [3, 5])
+@pytest.mark.parametrize("name", ["uniform2k_full", "ragged_near_camera", "clusters200k_crop"])
+def test_host_emulated_trig_forward_matches_oracle(emulator, tmp_path, name, N):
+    """Trigonometric moments (Eq. 13-14) and their circle bounds: the device
+    functions built for the host against the oracle's trigonometric path."""
+    sc, cam, region = _case(name)
+    rgb, T, Tq = emulate(emulator, tmp_path, sc, cam, region, n_intervals=N, basis=1)
+    ref = O.render(sc, cam, oracle_config(n_intervals=N, basis="trig"), region=region, probes=PROBES)
+    e_rgb = float(np.abs(rgb - ref["rgb"].numpy()).max())
+    e_T = float(np.abs(T - ref["T"].numpy()).max())
+    e_Tq = float(np.abs(Tq - np.exp(-ref["tau_probe"].numpy())).max())
+    print("host-emulated trig", name, N, "rgb %.2e T %.2e T(eta) %.2e" % (e_rgb, e_T, e_Tq))
+    assert np.isfinite(rgb).all() and np.isfinite(Tq).all()
+    assert e_rgb <= TOL and e_T <= TOL, (name, N, e_rgb, e_T)
+    # T(eta) at fixed probes: nearly atomic pixels (|m1/m0| ~ 0.994) make the
+    # circle bounds ill-conditioned; there the oracle itself moves tau by
+    # 1.7e-4 when its FP64 moments are perturbed by 1e-7 (relative), so the
+    # FP32 moments decide the fourth digit of such probes.
+    assert e_Tq <= 5e-4, (name, N, e_Tq)
 
 
 NAMES = ["means", "scales", "quats", "weights", "sh"]
