@@ -333,7 +333,8 @@ def run_single(args, dist, rank, world, dev):
     from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
     sc, cam = scenes.workload(args.workload)
     npix = cam.width * cam.height
-    R = Rasterizer(RasterConfig(basis=args.basis, n_intervals=args.n_intervals), device=dev)
+    R = Rasterizer(RasterConfig(basis=args.basis, n_intervals=args.n_intervals, moment_dtype=args.moment_dtype),
+                   device=dev)
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
     with_bwd = not args.forward_only and args.basis == "power"   # the trigonometric basis is forward only
@@ -413,7 +414,7 @@ def run_single(args, dist, rank, world, dev):
         fwd_mpix_s=world * npix / (fwd_ms * 1e-3) / 1e6,
         config={"workload": args.workload, "gaussians": g.P, "width": cam.width, "height": cam.height,
                 "sh_degree": sc.sh_degree,
-                "n_moments": 9, "n_intervals": n_int, "basis": args.basis,
+                "n_moments": 9, "n_intervals": n_int, "basis": args.basis, "moment_storage": args.moment_dtype,
                 "pass": "forward+backward (L2 loss vs random target)" if with_bwd else "forward",
                 "saved_queries": fr.qcap > 0,
                 "tiling": dict(tile=[R.config.tile_w, R.config.tile_h], batch=R.config.batch,
@@ -607,6 +608,8 @@ def main():
     ap.add_argument("--basis", default="power", choices=["power", "trig"],
                     help="moment basis; trig (Eq. 13-14) is forward only and reports no roofline")
     ap.add_argument("--n-intervals", type=int, default=3)
+    ap.add_argument("--moment-dtype", default="f32", choices=["f32", "bf16", "f16"],
+                    help="storage of the per-pixel moments (accumulation is FP32 in every case)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

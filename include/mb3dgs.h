@@ -90,9 +90,10 @@ typedef struct mb3dgs_config {
     /* Execution shape (no effect on the results: every pixel visits its
      * Gaussians in ascending id order whatever the tiling; mb3dgs_autotune
      * picks them).  tile_w x tile_h pixels per tile with tile_w * tile_h = 256,
-     * tile_w in {8, 16, 32, 64} (0, 0: 16 x 16); batch: Gaussian records staged
-     * in shared memory at a time, a multiple of 32 up to 256 (0: 256);
-     * schedule: MB3DGS_SCHEDULE_*. */
+     * tile_w in {8, 16, 32, 64} (0, 0: 16 x 16); each warp of a tile works
+     * on an 8 x 4 footprint and stages the records that overlap it in chunks
+     * of 32; batch: validated (a multiple of 32 up to 256, 0 = 256) but no
+     * longer used by the kernels; schedule: MB3DGS_SCHEDULE_*. */
     int tile_w, tile_h;
     int batch;
     int schedule;
@@ -273,12 +274,12 @@ int mb3dgs_get_pair_counts(const void* ws, size_t ws_bytes, int64_t* tile_pairs,
                            mb3dgs_stream_t stream);
 
 /* Autotuner of the execution shape (the paper has none; its tiling is its
- * own hardware's).  For each candidate tile shape (16x16, 32x8, 8x32), batch
- * (64, 128, 256) and schedule (QUEUE, GRID) whose workspace fits ws_bytes it
+ * own hardware's).  For each candidate tile shape (16x16, 32x8, 8x32) and
+ * schedule (QUEUE, GRID) whose workspace fits ws_bytes it
  * counts the frame's pairs, renders once untimed and times mb3dgs_render --
  * and mb3dgs_backward when d_dL_drgb and grads are given -- with CUDA events
  * on the stream (best of two), then writes the fastest shape into
- * cfg->tile_w, tile_h, batch and schedule and its time in ms into *best_ms
+ * cfg->tile_w, tile_h and schedule (batch 0) and its time in ms into *best_ms
  * (may be NULL).  cfg->query_capacity is kept.  Outputs go to the caller's
  * d_rgb [pixel][3] and d_T_final [pixel]; the other fields of cfg and the
  * scene are those of the frames to be rendered.  The forward results of

@@ -28,6 +28,7 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Phi^-1(p) by bisection + Newton on Phi(x) = erfc(-x / sqrt 2) / 2 (double)
 static double inv_normal_cdf(double p) {
@@ -140,8 +141,10 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.order = take(sizeof(int) * (size_t)ntiles);
     L.sched = take(SCHED_BYTES);
     const int md = cfg ? cfg->moment_dtype : 0;
+    // 16-bit storage: m0 plane (FP32) then one 16-byte vector of 8 halves per pixel; the
+    // plane is padded to 16 bytes so that the vectors are aligned
     L.moments = take(md == MB3DGS_MOMENTS_F32 ? sizeof(float) * NMOM * (size_t)npix
-                                              : sizeof(float) * (size_t)npix + 2 * (NMOM - 1) * (size_t)npix);
+                                              : align16(sizeof(float) * (size_t)npix) + 16 * (size_t)npix);
     L.recon = take(sizeof(float) * RECON * (size_t)npix);
     L.saved = take(sizeof(float) * 4 * (size_t)npix);
     L.dm = take(sizeof(float) * NMOM * (size_t)npix);
@@ -503,7 +506,6 @@ int mb3dgs_autotune(mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_
     if (rc) return rc;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     static const int shapes[3][2] = {{16, 16}, {32, 8}, {8, 32}};
-    static const int batches[3] = {64, 128, 256};
     static const int schedules[2] = {MB3DGS_SCHEDULE_QUEUE, MB3DGS_SCHEDULE_GRID};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return MB3DGS_ERR_CUDA;
@@ -530,9 +532,7 @@ int mb3dgs_autotune(mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_
         int64_t cap = 0;
         if ((rc = mb3dgs_get_pair_counts(ws, ws_bytes, &cap, nullptr, stream)) != MB3DGS_OK) break;
         if (mb3dgs_workspace_size(&c, cams, n_views, g->P, cap, &need) != MB3DGS_OK || need > ws_bytes) continue;
-        for (int bi = 0; bi < 3 && rc == MB3DGS_OK; ++bi)
-            for (int ki = 0; ki < 2 && rc == MB3DGS_OK; ++ki) {
-                c.batch = batches[bi];
+        for (int ki = 0; ki < 2 && rc == MB3DGS_OK; ++ki) {
                 c.schedule = schedules[ki];
                 float t_min = -1.0f;
                 for (int it = 0; it < 3 && rc == MB3DGS_OK; ++it) {

@@ -2,9 +2,10 @@
 // preprocessing adjoint.  The rescaling derivative (Eq. 15) is folded into
 // the passes as in the paper's two-pass adjoint (Sec. 3.3, App. C "Adjoint
 // rendering"); the proxy rectangles and the culling are constants.
-// Per-Gaussian sums over pixels use a warp reduce-scatter, one shared-memory
-// accumulator per staged record and one global atomicAdd per (tile, record,
-// field).  Tiles come from the schedule of tile.cuh like the forward passes.
+// Per-Gaussian sums over pixels use a warp reduce-scatter per record and one
+// global atomicAdd per (warp footprint, record, field).  Work units (8x4
+// pixel footprints of a tile) come from the schedule of tile.cuh like the
+// forward passes.
 #include "backward.cuh"
 #include "preprocess.cuh"
 #include "tile.cuh"
@@ -17,15 +18,20 @@ __device__ __forceinline__ float load_m0(const Params& p, const void* moments, i
 
 constexpr int GSTRIDE = 28;   // floats per record gradient (NGRAD padded)
 
-// Adds one staged batch's per-record gradients (fields 0..nf-1, expanded from
-// the compact sums s_acc[k][nk]) to the record gradients.
-__device__ __forceinline__ void flush_batch(const float* s_rec, const float* s_acc, int nb, int nk, int nf,
-                                            const int32_t* __restrict__ ids, int first, int64_t rec_base,
-                                            float* __restrict__ grec) {
-    for (int q = threadIdx.x; q < nb * nf; q += TPB) {
+// Per-warp scratch of the adjoint passes: the staged records of one chunk
+// (tile.cuh) and their compact per-record sums.
+constexpr int WARP_BWD_FLOATS = WARP_STAGE_FLOATS + 32 * NK_QUAD;
+
+// Adds a chunk's per-record gradients (fields 0..nf-1, expanded from the
+// compact sums s_sum[k][nk] of the warp's m staged records) to the record
+// gradients: one atomicAdd per (footprint, record, non-zero field).
+__device__ __forceinline__ void flush_chunk(const float* s_buf, const float* s_sum, int m, int nk, int nf,
+                                            int64_t rec_base, float* __restrict__ grec) {
+    const int* s_ids = reinterpret_cast<const int*>(s_buf + 32 * REC);
+    for (int q = threadIdx.x & 31; q < m * nf; q += 32) {
         const int k = q / nf, f = q - k * nf;
-        const float v = expand_geometry(s_rec + k * REC, s_acc + k * nk, f);
-        if (v != 0.0f) atomicAdd(&grec[(rec_base + ids[first + k]) * GSTRIDE + f], v);
+        const float v = expand_geometry(s_buf + k * REC, s_sum + k * nk, f);
+        if (v != 0.0f) atomicAdd(&grec[(rec_base + s_ids[k]) * GSTRIDE + f], v);
     }
 }
 
@@ -33,7 +39,9 @@ __device__ __forceinline__ void flush_batch(const float* s_rec, const float* s_a
 // Per pair: the quadrature, penalty and bound-query adjoint.  The direct
 // derivatives go through the record geometry to the per-record gradients;
 // the bound derivatives sum into the pixel's Phi, written out as the moment
-// adjoint polynomial psi.
+// adjoint polynomial psi.  Warp-level units as in the forward passes: each
+// warp walks its footprint's records, reduces every record's compact sums
+// over its 32 pixels and adds them to the record gradients per chunk.
 template <int NI, bool SAVED>
 __global__ void __launch_bounds__(TPB, 2)
     k_bwd_quadrature(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
@@ -41,20 +49,20 @@ __global__ void __launch_bounds__(TPB, 2)
                      const StatusWords* sw, const float* __restrict__ recon, const void* __restrict__ moments,
                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
                      const float* __restrict__ dL_dP, const float* __restrict__ dL_dT, float* __restrict__ psi_out,
-                     float* __restrict__ grec,
-                     const int* __restrict__ pq_off, const float4* __restrict__ pq, int64_t qcap) {
+                     float* __restrict__ grec, const int* __restrict__ pq_off, const float4* __restrict__ pq,
+                     int64_t qcap) {
     extern __shared__ float4 s_raw[];
-    __shared__ int s_slot;
-    float* s_rec = reinterpret_cast<float*>(s_raw);
-    float* s_acc = s_rec + REC * p.batch;             // [batch][NK_QUAD] compact sums
+    float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_BWD_FLOATS;
+    float* s_sum = s_buf + WARP_STAGE_FLOATS;          // [32][NK_QUAD] compact sums of the chunk
     // saved queries exist only when the frame's pixel pairs fit the capacity
     // (the status word then carries MB3DGS_ERR_CAPACITY)
     const bool any = sw->n_valid != 0 && !(SAVED && sw->n_pixpairs > (unsigned long long)qcap);
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
     const float4* q_end = SAVED ? pq + (size_t)qcap * nq : nullptr;   // end of the saved queries
     const int ridx = rs_index<NK_QUAD>(threadIdx.x & 31);   // compact sum this lane reduces
-    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
-        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
+    int fp, fx0, fy0;
+    for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
+        PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
         const float4* qp = nullptr;
         Recon R;
@@ -72,15 +80,16 @@ __global__ void __launch_bounds__(TPB, 2)
             if (dL_dT) pa.gm0 -= expf(-m0) * dL_dT[c.pix];   // T_final = e^{-m0}
             if (SAVED) qp = pq + (size_t)pq_off[c.pix] * nq;
         }
-        const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-        for (int b = 0; b * p.batch < n; ++b) {
-            for (int q = threadIdx.x; q < p.batch * NK_QUAD; q += TPB) s_acc[q] = 0.0f;
-            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
-            for (int k = 0; k < nb; ++k) {
-                const float* r = s_rec + k * REC;
+        for (int pos = c.start; pos < c.end; pos += 32) {
+            const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
+            for (int k = 0; k < m; ++k) {
+                const float* r = s_buf + k * REC;
                 const bool active = c.inside && rect_contains(r, c.px, c.py);
-                if (!__any_sync(0xffffffffu, active)) continue;
+                if (!__any_sync(0xffffffffu, active)) {
+                    if (ridx >= 0) s_sum[k * NK_QUAD + ridx] = 0.0f;
+                    continue;
+                }
                 float acc[NK_QUAD];
 #pragma unroll
                 for (int f = 0; f < NK_QUAD; ++f) acc[f] = 0.0f;
@@ -100,11 +109,10 @@ __global__ void __launch_bounds__(TPB, 2)
                     acc[K_RGB + 2] = pa.gS[2] * po.O;
                 }
                 const float v = reduce_scatter<NK_QUAD>(acc);
-                if (ridx >= 0 && v != 0.0f) atomicAdd(&s_acc[k * NK_QUAD + ridx], v);
+                if (ridx >= 0) s_sum[k * NK_QUAD + ridx] = v;
             }
-            __syncthreads();
-            flush_batch(s_rec, s_acc, nb, NK_QUAD, NGRAD, ids, c.start + b * p.batch, c.rec_base, grec);
-            __syncthreads();
+            __syncwarp();
+            flush_chunk(s_buf, s_sum, m, NK_QUAD, NGRAD, c.rec_base, grec);
         }
         if (c.inside) {
             float psi[NPOLY];
@@ -127,13 +135,13 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
                   const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWords* sw,
                   const float* __restrict__ recon, const float* __restrict__ psi_in, float* __restrict__ grec) {
     extern __shared__ float4 s_raw[];
-    __shared__ int s_slot;
-    float* s_rec = reinterpret_cast<float*>(s_raw);
-    float* s_acc = s_rec + REC * p.batch;             // [batch][NK_MOM] compact sums
+    float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_BWD_FLOATS;
+    float* s_sum = s_buf + WARP_STAGE_FLOATS;          // [32][NK_MOM] compact sums of the chunk
     const bool any = sw->n_valid != 0;
     const int lane = threadIdx.x & 31;
-    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
-        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
+    int fp, fx0, fy0;
+    for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
+        PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
         Recon R;                                      // only the standardisation (c, 1/s) is used
         float psi[NPOLY];
@@ -143,15 +151,16 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
 #pragma unroll
             for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
         }
-        const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-        for (int b = 0; b * p.batch < n; ++b) {
-            for (int q = threadIdx.x; q < p.batch * NK_MOM; q += TPB) s_acc[q] = 0.0f;
-            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
-            for (int k = 0; k < nb; ++k) {
-                const float* r = s_rec + k * REC;
+        for (int pos = c.start; pos < c.end; pos += 32) {
+            const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
+            for (int k = 0; k < m; ++k) {
+                const float* r = s_buf + k * REC;
                 const bool active = c.inside && rect_contains(r, c.px, c.py);
-                if (!__any_sync(0xffffffffu, active)) continue;
+                if (!__any_sync(0xffffffffu, active)) {
+                    if (lane < NK_MOM) s_sum[k * NK_MOM + lane] = 0.0f;
+                    continue;
+                }
                 float acc[NK_MOM];
 #pragma unroll
                 for (int f = 0; f < NK_MOM; ++f) acc[f] = 0.0f;
@@ -163,11 +172,10 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
                     geometry_adjoint_compact(r, dx, dy, c.rlen, g, g_mu, g_Sig, g_what, acc);
                 }
                 const float v = reduce_scatter16(acc);
-                if (lane < NK_MOM && v != 0.0f) atomicAdd(&s_acc[k * NK_MOM + lane], v);
+                if (lane < NK_MOM) s_sum[k * NK_MOM + lane] = v;
             }
-            __syncthreads();
-            flush_batch(s_rec, s_acc, nb, NK_MOM, G_RGB, ids, c.start + b * p.batch, c.rec_base, grec);
-            __syncthreads();
+            __syncwarp();
+            flush_chunk(s_buf, s_sum, m, NK_MOM, G_RGB, c.rec_base, grec);
         }
     }
 }
@@ -345,11 +353,11 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
     float* grec = reinterpret_cast<float*>(ws + L.grec);
     if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (L.n_tiles == 0) return MB3DGS_OK;
-    const size_t smem = sizeof(float) * (REC + NK_QUAD) * p.batch;
+    const size_t smem = sizeof(float) * WARP_BWD_FLOATS * WARPS;
     const bool saved_q = L.qcap > 0;
     auto k1 = p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true> : k_bwd_quadrature<3, false>)
                                  : (saved_q ? k_bwd_quadrature<0, true> : k_bwd_quadrature<0, false>);
-    if (!allow_dynamic_smem((const void*)k1, sizeof(float) * (REC + NK_QUAD) * TPB)) return MB3DGS_ERR_CUDA;
+    if (!allow_dynamic_smem((const void*)k1, smem)) return MB3DGS_ERR_CUDA;
     const TileLaunch t1 = tile_launch(p, L, ws, Q_BWD_QUAD, (const void*)k1, smem, st);
     count_launch();
     k1<<<t1.grid, TPB, smem, st>>>(
@@ -365,8 +373,8 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
 // Pass 2.
 int launch_backward_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
     if (L.n_tiles == 0) return MB3DGS_OK;
-    const size_t smem = sizeof(float) * (REC + NK_MOM) * p.batch;
-    if (!allow_dynamic_smem((const void*)k_bwd_moments, sizeof(float) * (REC + NK_MOM) * TPB)) return MB3DGS_ERR_CUDA;
+    const size_t smem = sizeof(float) * WARP_BWD_FLOATS * WARPS;
+    if (!allow_dynamic_smem((const void*)k_bwd_moments, smem)) return MB3DGS_ERR_CUDA;
     const TileLaunch t2 = tile_launch(p, L, ws, Q_BWD_MOM, (const void*)k_bwd_moments, smem, st);
     count_launch();
     k_bwd_moments<<<t2.grid, TPB, smem, st>>>(

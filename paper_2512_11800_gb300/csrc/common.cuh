@@ -108,7 +108,7 @@ struct Layout {
     size_t vals[2];     // int32  [cap]
     size_t hist;        // uint32 [256][nb_sort]
     size_t ranges;      // int32 [T][2]
-    size_t moments;     // F32: float [9][NPIX]; 16-bit: float [NPIX] + u16 [8][NPIX]
+    size_t moments;     // F32: float [9][NPIX]; 16-bit: float [NPIX], then 16-B aligned uint4 [NPIX] (8 halves a pixel)
     size_t recon;       // float [RECON][NPIX]
     size_t saved;       // float [4][NPIX]: sum L (3), O
     size_t dm;          // float [9][NPIX] adjoint moments (backward)
@@ -200,10 +200,10 @@ MB_HD Gauss1D pair_gaussian(const float* __restrict__ r, float dx, float dy, flo
     const float gz = fmaf(dy, r[R_MY + 2], fmaf(dx, r[R_MX + 2], r[R_GA + 2]));
     float dd = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     float od = fmaf(dy, r[R_OY], fmaf(dx, r[R_OX], r[R_O0]));
-    float inv = 1.0f / dd;
+    float inv = fdiv_(1.0f, dd);
     Gauss1D g;
     g.Sig2 = r2 * inv;
-    g.Sig = sqrtf(g.Sig2);
+    g.Sig = g.Sig2 * rsqrt_(g.Sig2);      // Sigma^2 > 0: |d_g|^2 of a finite record is positive
     g.mu = -od * rlen * inv;
     g.what = expf(fmaf(-0.5f * cross2, inv, r[R_LNW]));
     return g;
@@ -313,14 +313,16 @@ MB_HD void kernel_monomials(const Recon& R, const float e[5], float c[5]) {
 }
 
 // One Laguerre step for a degree-4 polynomial with value f, f' and f''.
+// The square root is approximate (it sets the step; the residual f of the
+// next evaluation sets the root).  den = f' - q or f' + q signed with f, the
+// denominator towards the neighbouring root on the chosen side.  The clamp to
+// [lo, hi] also maps a non-finite step (den = 0) into the bracket.
 MB_HD float laguerre_step(float x, float f, float fp, float fpp, float lo, float hi, bool right) {
-    const float q = sqrtf(fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 0.0f));
-    const float sq = f >= 0.0f ? q : -q;
-    const float den = right ? fp - sq : fp + sq;
-    const float step = den != 0.0f ? fdiv_(4.0f * f, den) : 0.0f;
-    float xn = x - step;
-    xn = fminf(fmaxf(xn, lo), hi);
-    return isfinite(xn) ? xn : x;
+    const float v = fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 1e-30f);
+    const float q = v * rsqrt_(v);
+    const float den = fp + copysignf(q, right ? -f : f);
+    const float xn = x - (f != 0.0f ? fdiv_(4.0f * f, den) : 0.0f);
+    return fminf(fmaxf(xn, lo), hi);
 }
 
 // Laguerre iteration towards the neighbouring root on one side.  For a

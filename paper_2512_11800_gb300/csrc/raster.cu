@@ -14,6 +14,9 @@
 namespace mb {
 
 // ---------------------------------------------------------------- moment pass
+// 16-bit storage: the FP32 m0 plane, then (16-byte aligned) one uint4 of
+// eight 16-bit scaled moments per pixel.
+__device__ __forceinline__ size_t packed_offset(int64_t npix) { return ((size_t)npix * 4 + 15) & ~(size_t)15; }
 __device__ __forceinline__ void store_moments(const Params& p, const float acc[NMOM], int64_t npix, int64_t pix,
                                               void* __restrict__ moments) {
     if (p.moment_dtype == MB3DGS_MOMENTS_F32) {
@@ -21,24 +24,25 @@ __device__ __forceinline__ void store_moments(const Params& p, const float acc[N
 #pragma unroll
         for (int k = 0; k < NMOM; ++k) m[k * npix + pix] = acc[k];
     } else {
-        // m0 in FP32, I_k / m0 (k >= 1; |.| <~ 1) in 16 bits: per-pixel scaling
+        // m0 in FP32, I_k / m0 (k >= 1; |.| <~ 1) in 16 bits: per-pixel scaling;
+        // a pixel's eight 16-bit values are one 16-byte vector store
         float* m0 = reinterpret_cast<float*>(moments);
         m0[pix] = acc[0];
         const float inv = acc[0] > 0.0f ? 1.0f / acc[0] : 0.0f;
-        uint16_t* h = reinterpret_cast<uint16_t*>(m0 + npix);
+        uint32_t w[4];
 #pragma unroll
-        for (int k = 1; k < NMOM; ++k) {
-            const float x = acc[k] * inv;
-            uint16_t bits;
+        for (int k = 0; k < 4; ++k) {
+            const float x0 = acc[2 * k + 1] * inv, x1 = acc[2 * k + 2] * inv;
             if (p.moment_dtype == MB3DGS_MOMENTS_BF16) {
-                __nv_bfloat16 hb = __float2bfloat16_rn(x);
-                bits = *reinterpret_cast<uint16_t*>(&hb);
+                const __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
+                w[k] = *reinterpret_cast<const uint32_t*>(&v);
             } else {
-                __half hh = __float2half_rn(x);
-                bits = *reinterpret_cast<uint16_t*>(&hh);
+                const __half2 v = __floats2half2_rn(x0, x1);
+                w[k] = *reinterpret_cast<const uint32_t*>(&v);
             }
-            h[(k - 1) * npix + pix] = bits;
         }
+        reinterpret_cast<uint4*>(static_cast<char*>(moments) + packed_offset(npix))[pix] =
+            make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -89,19 +93,15 @@ __device__ __forceinline__ void load_moments(const Params& p, const void* __rest
     } else {
         const float* m0 = reinterpret_cast<const float*>(moments);
         I[0] = m0[pix];
-        const uint16_t* h = reinterpret_cast<const uint16_t*>(m0 + npix);
+        const uint4 v = reinterpret_cast<const uint4*>(static_cast<const char*>(moments) + packed_offset(npix))[pix];
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-        for (int k = 1; k < NMOM; ++k) {
-            uint16_t bits = h[(k - 1) * npix + pix];
-            float x;
-            if (p.moment_dtype == MB3DGS_MOMENTS_BF16) {
-                __nv_bfloat16 hb = *reinterpret_cast<__nv_bfloat16*>(&bits);
-                x = __bfloat162float(hb);
-            } else {
-                __half hh = *reinterpret_cast<__half*>(&bits);
-                x = __half2float(hh);
-            }
-            I[k] = x * I[0];
+        for (int k = 0; k < 4; ++k) {
+            float2 x;
+            if (p.moment_dtype == MB3DGS_MOMENTS_BF16) x = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
+            else x = __half22float2(*reinterpret_cast<const __half2*>(&w[k]));
+            I[2 * k + 1] = x.x * I[0];
+            I[2 * k + 2] = x.y * I[0];
         }
     }
 }

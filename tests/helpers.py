@@ -94,3 +94,37 @@ def oracle_losses(tasks):
     ctx = multiprocessing.get_context("spawn")
     with ProcessPoolExecutor(max_workers=workers, mp_context=ctx, initializer=_worker_init) as ex:
         return list(ex.map(_loss_task, tasks, chunksize=4))
+
+
+def probe_excess(T_got, ref, probes, cfg, rel=2e-6, trials=16, seed=0):
+    """Transmittance probes T(eta) against the oracle, judged against the
+    oracle's own conditioning: for every pixel whose error exceeds 1e-4 the
+    oracle's optical depths are recomputed with every one of its FP64 moments
+    perturbed by rel * m0 (rel = 2e-6: the rounding of a FP32 sum of a few
+    hundred terms whose magnitudes add up to about m0, sqrt(n) eps m0 plus
+    each term's own rounding) and the largest change of T is that pixel's
+    allowance.  Returns the largest
+    error in excess of 1e-4 + allowance (<= 0 when every probe passes) and
+    the number of pixels that needed an allowance."""
+    import torch
+    T_ref = np.exp(-ref["tau_probe"].numpy())
+    err = np.abs(T_got - T_ref).max(-1)
+    bad = np.argwhere(err > 1e-4)
+    worst = float(err.max()) - 1e-4 if bad.size == 0 else -1.0
+    depth = O.trig_optical_depth if cfg.basis == "trig" else O.optical_depth
+    rng = np.random.default_rng(seed)
+    eta = torch.as_tensor(np.asarray(probes, dtype=np.float64))[None]
+    for iy, ix in bad:
+        m = ref["m"][iy, ix][None]
+        base = np.exp(-depth(m, eta, cfg).numpy()[0])
+        spread = 0.0
+        for _ in range(trials):
+            noise = torch.as_tensor(rng.normal(size=m.shape))
+            if m.is_complex():
+                im = torch.as_tensor(rng.normal(size=m.shape))
+                im[..., 0] = 0.0                      # m0 is real
+                noise = torch.complex(noise, im)
+            pm = m + rel * m[..., :1].real * noise
+            spread = max(spread, float(np.abs(np.exp(-depth(pm, eta, cfg).numpy()[0]) - base).max()))
+        worst = max(worst, float(err[iy, ix]) - 1e-4 - spread)
+    return worst, len(bad)

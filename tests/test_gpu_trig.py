@@ -3,11 +3,11 @@ App. C "Trigonometric Moments"): the CUDA path through the C ABI against the
 oracle's trigonometric path.
 
 Bar: 1e-4 absolute on RGB and final transmittance, at N = 3 and N = 5
-intervals.  The transmittance T(eta) at fixed probe depths is held to 5e-4:
-for nearly atomic pixels (|m1/m0| close to 1) the circle bounds are so
-ill-conditioned that the oracle itself moves tau by ~1.7e-4 when its FP64
-moments are perturbed by 1e-7 (relative), so the FP32 moments decide the
-fourth digit there.  The adjoint is not implemented for this basis: the
+intervals.  The transmittance T(eta) at fixed probe depths is held to 1e-4
+plus, for nearly atomic pixels (|m1/m0| close to 1, where the circle bounds
+are ill-conditioned and the FP32 moments decide the fourth digit), the change
+of the oracle's own T(eta) under a 2e-6 (of m0) perturbation of its moments
+(helpers.probe_excess).  The adjoint is not implemented for this basis: the
 backward entry point reports MB3DGS_ERR_UNSUPPORTED.
 """
 import os
@@ -23,7 +23,6 @@ from helpers import oracle_config
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
-TOL_PROBE = 5e-4
 torch.set_num_threads(os.cpu_count() or 8)
 PROBES = np.linspace(0.0, 1.0, 17)
 
@@ -55,18 +54,23 @@ def _errors(out, ref, cam, region=None):
 
 
 @pytest.mark.parametrize("N", [3, 5])
-def test_trig_uniform2k_full_image(N):
+def test_trig_uniform2k(N):
+    """The 2k-Gaussian 128x128 frame, checked on its 64x64 centre (where the
+    scene is): image, transmittance probes and the moments themselves."""
     R = _rasterizer(N)
     sc, cam = scenes.workload("uniform2k_128")
     npix = cam.width * cam.height
     eta = torch.tensor(PROBES, dtype=torch.float32, device="cuda").expand(npix, -1).contiguous()
     out = R.render_staged(G(sc), cam, eta=eta)
-    ref = O.render(sc, cam, oracle_config(R.config), probes=PROBES)
-    err = _errors(out, ref, cam)
-    print("trig uniform2k N=%d max errors" % N, err)
-    assert err["rgb"] <= TOL and err["T"] <= TOL and err["T_eta"] <= TOL_PROBE, err
+    region = (32, 32, 64, 64)
+    ref = O.render(sc, cam, oracle_config(R.config), probes=PROBES, region=region)
+    err = _errors(out, ref, cam, region)
+    sl = (slice(32, 96), slice(32, 96))
+    excess, n_allow = helpers.probe_excess(_img(out["T_eta"], cam)[sl], ref, PROBES, oracle_config(R.config))
+    print("trig uniform2k N=%d max errors" % N, err, "pixels judged by conditioning", n_allow)
+    assert err["rgb"] <= TOL and err["T"] <= TOL and excess <= 0.0, (err, excess)
     # the staged moment output is the trigonometric moments {m0, Re m_k, Im m_k}
-    m = _img(out["moments"], cam)
+    m = _img(out["moments"], cam)[sl]
     mr = ref["m"].numpy()
     mo = np.concatenate([mr[..., :1].real, np.stack([mr[..., 1:].real, mr[..., 1:].imag], -1).reshape(
         mr.shape[0], mr.shape[1], -1)], -1)

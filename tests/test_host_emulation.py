@@ -145,14 +145,17 @@ def test_host_emulated_trig_forward_matches_oracle(emulator, tmp_path, name, N):
     e_rgb = float(np.abs(rgb - ref["rgb"].numpy()).max())
     e_T = float(np.abs(T - ref["T"].numpy()).max())
     e_Tq = float(np.abs(Tq - np.exp(-ref["tau_probe"].numpy())).max())
-    print("host-emulated trig", name, N, "rgb %.2e T %.2e T(eta) %.2e" % (e_rgb, e_T, e_Tq))
+    # T(eta) at fixed probes: 1e-4, plus, for nearly atomic pixels (|m1/m0|
+    # ~ 0.99), the change of the oracle's own T(eta) under a 2e-6 (of m0)
+    # perturbation of its moments (the circle bounds are ill-conditioned
+    # there, and FP32 moments decide the fourth digit)
+    import helpers
+    excess, n_allow = helpers.probe_excess(Tq, ref, PROBES, oracle_config(n_intervals=N, basis="trig"))
+    print("host-emulated trig", name, N, "rgb %.2e T %.2e T(eta) %.2e (%d pixels judged by conditioning)"
+          % (e_rgb, e_T, e_Tq, n_allow))
     assert np.isfinite(rgb).all() and np.isfinite(Tq).all()
     assert e_rgb <= TOL and e_T <= TOL, (name, N, e_rgb, e_T)
-    # T(eta) at fixed probes: nearly atomic pixels (|m1/m0| ~ 0.994) make the
-    # circle bounds ill-conditioned; there the oracle itself moves tau by
-    # 1.7e-4 when its FP64 moments are perturbed by 1e-7 (relative), so the
-    # FP32 moments decide the fourth digit of such probes.
-    assert e_Tq <= 5e-4, (name, N, e_Tq)
+    assert excess <= 0.0, (name, N, e_Tq, excess)
 
 
 NAMES = ["means", "scales", "quats", "weights", "sh"]
