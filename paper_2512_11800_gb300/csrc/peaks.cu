@@ -36,13 +36,15 @@ __global__ void __launch_bounds__(PROBE_TPB) k_probe_ffma(float* __restrict__ si
 }
 
 // One MUFU instruction per chain step; the operand negation is a free source
-// modifier, so x <- 2^-x and x <- rsqrt(x) stay finite and bounded.
+// modifier, so x <- 2^-x and x <- rsqrt(x) stay finite and bounded.  The
+// reciprocal chain is x <- 1/(x + 1) (an FADD on the FMA pipe beside each
+// MUFU): x <- 1/x would let the compiler cancel pairs of reciprocals.
 template <int OP>
 __device__ __forceinline__ float mufu_op(float x) {
     float y;
     if (OP == 0) asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
     else if (OP == 1) asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    else if (OP == 2) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    else if (OP == 2) asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x + 1.0f));
     else asm volatile("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
