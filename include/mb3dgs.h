@@ -90,10 +90,11 @@ typedef struct mb3dgs_config {
     /* Execution shape (no effect on the results: every pixel visits its
      * Gaussians in ascending id order whatever the tiling; mb3dgs_autotune
      * picks them).  tile_w x tile_h pixels per tile with tile_w * tile_h = 256,
-     * tile_w in {8, 16, 32, 64} (0, 0: 16 x 16); each warp of a tile works
-     * on an 8 x 4 footprint and stages the records that overlap it in chunks
-     * of 32; batch: validated (a multiple of 32 up to 256, 0 = 256) but no
-     * longer used by the kernels; schedule: MB3DGS_SCHEDULE_*. */
+     * tile_w in {8, 16, 32, 64} (0, 0: 16 x 16); in every pass but the
+     * moment adjoint each warp of a tile works on an 8 x 4 footprint and
+     * stages the records that overlap it in chunks of 32; batch: records
+     * staged per CTA batch in the moment-adjoint pass, a multiple of 32 up to
+     * 256 (0: 256); schedule: MB3DGS_SCHEDULE_*. */
     int tile_w, tile_h;
     int batch;
     int schedule;

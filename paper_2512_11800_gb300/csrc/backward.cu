@@ -2,10 +2,10 @@
 // preprocessing adjoint.  The rescaling derivative (Eq. 15) is folded into
 // the passes as in the paper's two-pass adjoint (Sec. 3.3, App. C "Adjoint
 // rendering"); the proxy rectangles and the culling are constants.
-// Per-Gaussian sums over pixels use a warp reduce-scatter per record and one
-// global atomicAdd per (warp footprint, record, field).  Work units (8x4
-// pixel footprints of a tile) come from the schedule of tile.cuh like the
-// forward passes.
+// Per-Gaussian sums over pixels use a warp reduce-scatter per record, then
+// one global atomicAdd per (warp footprint, record, field) in pass 1 and per
+// (tile, record, field) in pass 2.  Work comes from the schedule of tile.cuh
+// like the forward passes.
 #include "backward.cuh"
 #include "preprocess.cuh"
 #include "tile.cuh"
@@ -124,9 +124,25 @@ __global__ void __launch_bounds__(TPB, 2)
     }
 }
 
+// Adds one staged batch's per-record gradients (fields 0..nf-1, expanded from
+// the compact sums s_acc[k][nk]) to the record gradients.
+__device__ __forceinline__ void flush_batch(const float* s_rec, const float* s_acc, int nb, int nk, int nf,
+                                            const int32_t* __restrict__ ids, int first, int64_t rec_base,
+                                            float* __restrict__ grec) {
+    for (int q = threadIdx.x; q < nb * nf; q += TPB) {
+        const int k = q / nf, f = q - k * nf;
+        const float v = expand_geometry(s_rec + k * REC, s_acc + k * nk, f);
+        if (v != 0.0f) atomicAdd(&grec[(rec_base + ids[first + k]) * GSTRIDE + f], v);
+    }
+}
+
 // ---------------------------------------------------------------- pass 2
 // Per pair: int psi d(d mu_i) through the reverse sweep of the moment
-// recurrence, chained to the record geometry (fields before G_RGB).
+// recurrence, chained to the record geometry (fields before G_RGB).  One CTA
+// works on one tile at a time with record batches staged for the whole CTA:
+// its per-record sums are combined over the tile's 256 pixels in shared
+// memory before the global atomics (one per tile, record and field), which
+// measured faster than per-footprint flushes for this light pass.
 #ifndef MB_BWD_MOMENTS_MIN_CTAS
 #define MB_BWD_MOMENTS_MIN_CTAS 4
 #endif
@@ -135,13 +151,13 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
                   const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWords* sw,
                   const float* __restrict__ recon, const float* __restrict__ psi_in, float* __restrict__ grec) {
     extern __shared__ float4 s_raw[];
-    float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_BWD_FLOATS;
-    float* s_sum = s_buf + WARP_STAGE_FLOATS;          // [32][NK_MOM] compact sums of the chunk
+    __shared__ int s_slot;
+    float* s_rec = reinterpret_cast<float*>(s_raw);
+    float* s_acc = s_rec + REC * p.batch;             // [batch][NK_MOM] compact sums
     const bool any = sw->n_valid != 0;
     const int lane = threadIdx.x & 31;
-    int fp, fx0, fy0;
-    for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
-        PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
+    for (int64_t tile = next_tile(ts, &s_slot, true); tile >= 0; tile = next_tile(ts, &s_slot, false)) {
+        PixelCtx c = pixel_ctx(vt, ranges, P, tile);
         if (!any) c.end = c.start;
         Recon R;                                      // only the standardisation (c, 1/s) is used
         float psi[NPOLY];
@@ -151,16 +167,15 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
 #pragma unroll
             for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
         }
+        const int n = c.end - c.start;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-        for (int pos = c.start; pos < c.end; pos += 32) {
-            const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
-            for (int k = 0; k < m; ++k) {
-                const float* r = s_buf + k * REC;
+        for (int b = 0; b * p.batch < n; ++b) {
+            for (int q = threadIdx.x; q < p.batch * NK_MOM; q += TPB) s_acc[q] = 0.0f;
+            const int nb = stage_batch(s_rec, rec, ids, c.rec_base, c.start, c.end, b, p.batch);
+            for (int k = 0; k < nb; ++k) {
+                const float* r = s_rec + k * REC;
                 const bool active = c.inside && rect_contains(r, c.px, c.py);
-                if (!__any_sync(0xffffffffu, active)) {
-                    if (lane < NK_MOM) s_sum[k * NK_MOM + lane] = 0.0f;
-                    continue;
-                }
+                if (!__any_sync(0xffffffffu, active)) continue;
                 float acc[NK_MOM];
 #pragma unroll
                 for (int f = 0; f < NK_MOM; ++f) acc[f] = 0.0f;
@@ -172,10 +187,11 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
                     geometry_adjoint_compact(r, dx, dy, c.rlen, g, g_mu, g_Sig, g_what, acc);
                 }
                 const float v = reduce_scatter16(acc);
-                if (lane < NK_MOM) s_sum[k * NK_MOM + lane] = v;
+                if (lane < NK_MOM && v != 0.0f) atomicAdd(&s_acc[k * NK_MOM + lane], v);
             }
-            __syncwarp();
-            flush_chunk(s_buf, s_sum, m, NK_MOM, G_RGB, c.rec_base, grec);
+            __syncthreads();
+            flush_batch(s_rec, s_acc, nb, NK_MOM, G_RGB, ids, c.start + b * p.batch, c.rec_base, grec);
+            __syncthreads();
         }
     }
 }
@@ -373,8 +389,8 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
 // Pass 2.
 int launch_backward_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
     if (L.n_tiles == 0) return MB3DGS_OK;
-    const size_t smem = sizeof(float) * WARP_BWD_FLOATS * WARPS;
-    if (!allow_dynamic_smem((const void*)k_bwd_moments, smem)) return MB3DGS_ERR_CUDA;
+    const size_t smem = sizeof(float) * (REC + NK_MOM) * p.batch;
+    if (!allow_dynamic_smem((const void*)k_bwd_moments, sizeof(float) * (REC + NK_MOM) * TPB)) return MB3DGS_ERR_CUDA;
     const TileLaunch t2 = tile_launch(p, L, ws, Q_BWD_MOM, (const void*)k_bwd_moments, smem, st);
     count_launch();
     k_bwd_moments<<<t2.grid, TPB, smem, st>>>(

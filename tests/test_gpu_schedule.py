@@ -95,7 +95,7 @@ def test_autotune_keeps_the_images():
     R = _rast()
     ref = R.render(g, cam)["rgb"].clone()
     tw, th, batch, sched, ms = R.autotune(g, cam, backward=True)
-    assert (tw, th) in [(16, 16), (32, 8), (8, 32)] and batch in (64, 128, 256) and sched in ("queue", "grid")
+    assert (tw, th) in [(16, 16), (32, 8), (8, 32)] and batch in (0, 256) and sched in ("queue", "grid")
     assert ms > 0.0
     assert torch.equal(R.render(g, cam)["rgb"], ref)
     assert R.status()[0] == 0
