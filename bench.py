@@ -485,25 +485,21 @@ def run_batch16(args, dist, rank, world, dev):
     R._ws = None
     torch.cuda.empty_cache()
 
-    # batched: the views packed in order into groups whose saved bound queries
-    # fit the query budget (one group = one set of persistent launches over
-    # all its views' tiles), the whole step captured in one CUDA graph
-    limit = min(2 ** 31 - 1, int(R.config.query_budget_gb * 2 ** 30) // (16 * (R.config.n_intervals + 1)))
+    # batched: all 16 views in one frame (one set of persistent launches over
+    # all views' tiles), the whole step captured in one CUDA graph.  The
+    # bound queries are kept for as many pixels as the free device memory
+    # allows (60 % of it after the workspace); the backward solves the rest
+    # again.
     counts = [R.pair_counts(g, c) for c in cams]
-    groups, cur, cur_pp = [], [], 0
-    for i, (tp, pp) in enumerate(counts):
-        if cur and cur_pp + pp > limit:
-            groups.append(cur)
-            cur, cur_pp = [], 0
-        cur.append(i)
-        cur_pp += pp
-    groups.append(cur)
-    need = 0
-    for grp in groups:
-        gc = [cams[i] for i in grp]
-        tp, pp = R.pair_counts(g, gc)
-        R.set_query_capacity(pp)
-        need = max(need, R.workspace_bytes(gc, g.P, tp))
+    groups = [list(range(len(cams)))]
+    tp, pp = R.pair_counts(g, cams)
+    R.set_query_capacity(0)
+    base = R.workspace_bytes(cams, g.P, tp)
+    torch.cuda.empty_cache()
+    free = torch.cuda.mem_get_info(dev)[0]
+    R.config.query_budget_gb = max(0.0, 0.6 * (free - base)) / 2 ** 30
+    R.set_query_capacity(pp)
+    need = R.workspace_bytes(cams, g.P, tp)
     R._ws = None
     shared = R.workspace(need)
     fbs = [Frame(R, g, [cams[i] for i in grp], target[offs[grp[0]]:offs[grp[-1] + 1]], ws=shared)
@@ -578,9 +574,11 @@ def run_batch16(args, dist, rank, world, dev):
         higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
         config={"workload": "batch16_shells1M", "gaussians": g.P, "views": [[c.width, c.height] for c in cams],
                 "pixels": tot, "pass": "forward+backward" if with_bwd else "forward",
-                "saved_queries": all(f.qcap > 0 for f in fbs), "groups": groups,
+                "query_slots": fbs[0].qcap, "pixel_pairs": pp,
+                "kept_queries": "%.0f %% of the pixel pairs (60 %% of free device memory)" % (100.0 * fbs[0].qcap / max(pp, 1)),
+                "groups": groups,
                 "tiling": dict(tile=list(tuned[:2]), batch=tuned[2], schedule=tuned[3], tuned_ms=tuned[4]),
-                "graph": "whole step in one CUDA graph (one set of persistent launches per view group)",
+                "graph": "whole step in one CUDA graph (one set of persistent launches over all 16 views)",
                 "l2": "inputs larger than L2",
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         sequential=dict(ms_per_step=seq_ms, mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,

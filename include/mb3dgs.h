@@ -100,12 +100,15 @@ typedef struct mb3dgs_config {
     int schedule;
     int64_t query_capacity; /* (pixel, Gaussian) pair slots in which mb3dgs_shade keeps
                            the N+1 bound queries of every pair (16 (N+1) bytes a
-                           pair: 64 at N = 3) for
-                           mb3dgs_backward; 0 (default): backward recomputes them.
-                           Size it with the pixel-pair count of
-                           mb3dgs_get_pair_counts; a frame with more pairs sets
-                           MB3DGS_ERR_CAPACITY and saves none.  Ignored with
-                           the TRIG basis. */
+                           pair: 64 at N = 3) for mb3dgs_backward, which then
+                           reads them instead of solving them again.  Pixels
+                           are served in pixel order while all of a pixel's
+                           pairs fit; the backward solves the queries of the
+                           remaining pixels again (a memory / time trade the
+                           caller sets; the results are the same).  0 (default):
+                           all are recomputed; the pixel-pair count of
+                           mb3dgs_get_pair_counts keeps all.  Below 2^40.
+                           Ignored with the TRIG basis. */
     int basis;          /* MB3DGS_BASIS_*; default POWER */
     float trig_theta;   /* TRIG: wrapping angle theta in (0, 2 pi) (reading); pi/2 */
 } mb3dgs_config;

@@ -43,7 +43,7 @@ class RasterConfig:
     # keep every pair's bound queries from the forward for the backward
     # (64 B per (pixel, Gaussian) pair at N = 3); False: backward recomputes them
     save_queries: bool = True
-    query_budget_gb: float = 48.0  # saved queries only while they fit this (and < 2^31 pairs)
+    query_budget_gb: float = 48.0  # device memory for kept queries; pixels beyond it recompute theirs
     # execution shape (results do not depend on it; Rasterizer.autotune sets it)
     tile_w: int = 16
     tile_h: int = 16
@@ -221,13 +221,14 @@ class Rasterizer:
         return self.config.tile_w, self.config.tile_h, self.config.batch, self.config.schedule, float(ms.value)
 
     def set_query_capacity(self, n):
-        """Query slots of the following calls (0: backward recomputes the queries):
-        n when queries are saved and n pairs fit the budget, else 0."""
+        """Query slots of the following calls for a frame of n pixel pairs:
+        as many as the budget holds (0 without saved queries: the backward
+        solves every query again; pixels beyond the slots do so too)."""
         n = int(n)
-        nbytes = n * 16 * (self.config.n_intervals + 1)
-        fits = n < 2 ** 31 and nbytes <= self.config.query_budget_gb * 2 ** 30
-        keep = self.config.save_queries and fits and self.config.basis == "power"   # trig: forward only
-        self.cfg_c.query_capacity = n if keep else 0
+        per_pair = 16 * (self.config.n_intervals + 1)
+        budget = int(self.config.query_budget_gb * 2 ** 30) // per_pair
+        keep = self.config.save_queries and self.config.basis == "power"   # trig: forward only
+        self.cfg_c.query_capacity = min(n, budget) if keep else 0
         return int(self.cfg_c.query_capacity)
 
     def render(self, g: GaussianTensors, cams, capacity=None, stream=None, penalty=True, out=None,

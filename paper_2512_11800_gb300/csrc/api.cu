@@ -122,9 +122,9 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.sort_passes = (bits + 7) / 8;
     L.final_buf = L.sort_passes % 2;
     L.qcap = cfg && cfg->basis == MB3DGS_BASIS_POWER ? cfg->query_capacity : 0;
-    if (L.qcap < 0 || L.qcap >= (int64_t(1) << 31)) return MB3DGS_ERR_INVALID_ARG;
+    if (L.qcap < 0 || L.qcap >= (int64_t(1) << 40)) return MB3DGS_ERR_INVALID_ARG;
     L.scan_tmp_elems = std::max(scan_tmp_elems(L.VP), scan_tmp_elems((int64_t)256 * L.nb_sort));
-    if (L.qcap > 0) L.scan_tmp_elems = std::max(L.scan_tmp_elems, scan_tmp_elems(npix));
+    if (L.qcap > 0) L.scan_tmp_elems = std::max(L.scan_tmp_elems, 2 * scan_tmp_elems(npix));   // 64-bit scan
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align256(o + bytes); return r; };
     L.status = take(64);
@@ -151,7 +151,7 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.grec = take(sizeof(float) * 28 * (size_t)L.VP);
     if (L.qcap > 0) {
         L.npp = take(sizeof(int) * (size_t)npix);
-        L.pq_off = take(sizeof(int) * (size_t)npix);
+        L.pq_off = take(sizeof(long long) * (size_t)npix);
         L.pq = take(sizeof(float) * 4 * (size_t)(cfg->n_intervals + 1) * (size_t)L.qcap);   // one float4 a query
     }
     L.total = o;

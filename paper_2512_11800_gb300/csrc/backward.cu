@@ -42,6 +42,9 @@ __device__ __forceinline__ void flush_chunk(const float* s_buf, const float* s_s
 // adjoint polynomial psi.  Warp-level units as in the forward passes: each
 // warp walks its footprint's records, reduces every record's compact sums
 // over its 32 pixels and adds them to the record gradients per chunk.
+// SAVED: only the pixels whose bound queries the quadrature pass kept
+// (pq_off + npp <= qcap), read instead of solved; otherwise the pixels that
+// kept none (all pixels when qcap == 0), whose queries are solved again.
 template <int NI, bool SAVED>
 __global__ void __launch_bounds__(TPB, 2)
     k_bwd_quadrature(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
@@ -49,21 +52,24 @@ __global__ void __launch_bounds__(TPB, 2)
                      const StatusWords* sw, const float* __restrict__ recon, const void* __restrict__ moments,
                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
                      const float* __restrict__ dL_dP, const float* __restrict__ dL_dT, float* __restrict__ psi_out,
-                     float* __restrict__ grec, const int* __restrict__ pq_off, const float4* __restrict__ pq,
-                     int64_t qcap) {
+                     float* __restrict__ grec, const int* __restrict__ npp, const long long* __restrict__ pq_off,
+                     const float4* __restrict__ pq, int64_t qcap) {
     extern __shared__ float4 s_raw[];
     float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_BWD_FLOATS;
     float* s_sum = s_buf + WARP_STAGE_FLOATS;          // [32][NK_QUAD] compact sums of the chunk
-    // saved queries exist only when the frame's pixel pairs fit the capacity
-    // (the status word then carries MB3DGS_ERR_CAPACITY)
-    const bool any = sw->n_valid != 0 && !(SAVED && sw->n_pixpairs > (unsigned long long)qcap);
+    const bool any = sw->n_valid != 0;
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
     const float4* q_end = SAVED ? pq + (size_t)qcap * nq : nullptr;   // end of the saved queries
     const int ridx = rs_index<NK_QUAD>(threadIdx.x & 31);   // compact sum this lane reduces
     int fp, fx0, fy0;
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
         PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
-        if (!any) c.end = c.start;
+        long long off = 0;
+        if (c.inside && qcap > 0) {
+            off = pq_off[c.pix];
+            c.inside = (off + npp[c.pix] <= qcap) == SAVED;   // this launch's pixels
+        }
+        if (!any || !__any_sync(0xffffffffu, c.inside)) c.end = c.start;
         const float4* qp = nullptr;
         Recon R;
         PixelAdj pa;
@@ -78,7 +84,7 @@ __global__ void __launch_bounds__(TPB, 2)
             const float m0 = load_m0(p, moments, c.pix);
             pa = pixel_adjoint(p, m0, S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
             if (dL_dT) pa.gm0 -= expf(-m0) * dL_dT[c.pix];   // T_final = e^{-m0}
-            if (SAVED) qp = pq + (size_t)pq_off[c.pix] * nq;
+            if (SAVED) qp = pq + (size_t)off * nq;
         }
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         for (int pos = c.start; pos < c.end; pos += 32) {
@@ -370,19 +376,26 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
     if (cudaMemsetAsync(grec, 0, sizeof(float) * GSTRIDE * (size_t)L.VP, st) != cudaSuccess) return MB3DGS_ERR_CUDA;
     if (L.n_tiles == 0) return MB3DGS_OK;
     const size_t smem = sizeof(float) * WARP_BWD_FLOATS * WARPS;
-    const bool saved_q = L.qcap > 0;
-    auto k1 = p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true> : k_bwd_quadrature<3, false>)
-                                 : (saved_q ? k_bwd_quadrature<0, true> : k_bwd_quadrature<0, false>);
-    if (!allow_dynamic_smem((const void*)k1, smem)) return MB3DGS_ERR_CUDA;
-    const TileLaunch t1 = tile_launch(p, L, ws, Q_BWD_QUAD, (const void*)k1, smem, st);
-    count_launch();
-    k1<<<t1.grid, TPB, smem, st>>>(
-        p, vt, t1.ts, reinterpret_cast<const float*>(ws + L.rec),
-        reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
-        L.npix, reinterpret_cast<const StatusWords*>(ws + L.status), reinterpret_cast<const float*>(ws + L.recon),
-        ws + L.moments, reinterpret_cast<const float*>(ws + L.saved), dL_drgb, dL_dP, dL_dT,
-        reinterpret_cast<float*>(ws + L.dm), grec, saved_q ? reinterpret_cast<const int*>(ws + L.pq_off) : nullptr,
-        saved_q ? reinterpret_cast<const float4*>(ws + L.pq) : nullptr, L.qcap);
+    const bool kept = L.qcap > 0;
+    // with kept queries: one launch for the pixels that kept theirs, one for
+    // the rest (those beyond the capacity; the launch exits early when none)
+    for (int pass = kept ? 0 : 1; pass < 2; ++pass) {
+        const bool saved_q = pass == 0;
+        auto k1 = p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true> : k_bwd_quadrature<3, false>)
+                                     : (saved_q ? k_bwd_quadrature<0, true> : k_bwd_quadrature<0, false>);
+        if (!allow_dynamic_smem((const void*)k1, smem)) return MB3DGS_ERR_CUDA;
+        const TileLaunch t1 = tile_launch(p, L, ws, Q_BWD_QUAD, (const void*)k1, smem, st);
+        count_launch();
+        k1<<<t1.grid, TPB, smem, st>>>(
+            p, vt, t1.ts, reinterpret_cast<const float*>(ws + L.rec),
+            reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges),
+            L.P, L.npix, reinterpret_cast<const StatusWords*>(ws + L.status),
+            reinterpret_cast<const float*>(ws + L.recon), ws + L.moments, reinterpret_cast<const float*>(ws + L.saved),
+            dL_drgb, dL_dP, dL_dT, reinterpret_cast<float*>(ws + L.dm), grec,
+            kept ? reinterpret_cast<const int*>(ws + L.npp) : nullptr,
+            kept ? reinterpret_cast<const long long*>(ws + L.pq_off) : nullptr,
+            kept ? reinterpret_cast<const float4*>(ws + L.pq) : nullptr, L.qcap);
+    }
     return MB3DGS_OK;
 }
 

@@ -20,46 +20,51 @@ constexpr int SORT_CHUNK = SORT_TPB * SORT_ROUNDS;  // pairs per sort block
 constexpr int RADIX = 256;
 
 // ---------------------------------------------------------------- scans
-__device__ __forceinline__ int block_exclusive_scan(int v, int* s_warp, int* total) {
+// Exclusive scans of int counts into int (tile pairs, radix histograms) or
+// 64-bit (per-pixel offsets of the kept bound queries, whose total can pass
+// 2^31) offsets.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* s_warp, T* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
+        T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
         int nw = blockDim.x >> 5;
-        int w = lane < nw ? s_warp[lane] : 0;
+        T w = lane < nw ? s_warp[lane] : T(0);
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, w, o);
+            T y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
         if (lane < nw) s_warp[lane] = w;
     }
     __syncthreads();
-    int base = wid > 0 ? s_warp[wid - 1] : 0;
+    T base = wid > 0 ? s_warp[wid - 1] : T(0);
     if (total) *total = s_warp[(blockDim.x >> 5) - 1];
     __syncthreads();
     return base + x - v;
 }
 
 // out[i] = sum_{j<i} in[j] within each block chunk; block sums to sums[b]
-__global__ void k_scan_blocks(const int* __restrict__ in, int* __restrict__ out, int* __restrict__ sums, int64_t n) {
-    __shared__ int s_warp[32];
+template <typename Tin, typename T>
+__global__ void k_scan_blocks(const Tin* __restrict__ in, T* __restrict__ out, T* __restrict__ sums, int64_t n) {
+    __shared__ T s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
-    int vals[SCAN_ITEMS];
-    int local = 0;
+    T vals[SCAN_ITEMS];
+    T local = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        vals[k] = (base + k < n) ? in[base + k] : 0;
+        vals[k] = (base + k < n) ? (T)in[base + k] : T(0);
         local += vals[k];
     }
-    int total;
-    int pre = block_exclusive_scan(local, s_warp, &total);
+    T total;
+    T pre = block_exclusive_scan<T>(local, s_warp, &total);
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         if (base + k < n) out[base + k] = pre;
@@ -68,29 +73,39 @@ __global__ void k_scan_blocks(const int* __restrict__ in, int* __restrict__ out,
     if (threadIdx.x == 0 && sums) sums[blockIdx.x] = total;
 }
 
-__global__ void k_scan_add(int* __restrict__ out, const int* __restrict__ sums_scanned, int64_t n) {
+template <typename T>
+__global__ void k_scan_add(T* __restrict__ out, const T* __restrict__ sums_scanned, int64_t n) {
     const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
-    const int add = sums_scanned[blockIdx.x];
+    const T add = sums_scanned[blockIdx.x];
     for (int k = threadIdx.x; k < SCAN_CHUNK; k += blockDim.x)
         if (base + k < n) out[base + k] += add;
 }
 
-// Exclusive scan of n ints (in may equal out).  tmp holds the block sums of
-// every level: sum_l ceil(n / CHUNK^l) ints.
-void exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st) {
+// Exclusive scan of n values (in may equal out).  tmp holds the block sums of
+// every level: sum_l ceil(n / CHUNK^l) elements of T.
+template <typename Tin, typename T>
+static void exclusive_scan_t(const Tin* in, T* out, int64_t n, T* tmp, cudaStream_t st) {
     if (n <= 0) return;
     const int64_t nb = ceil_div64(n, SCAN_CHUNK);
     if (nb == 1) {
         count_launch();
-        k_scan_blocks<<<1, SCAN_TPB, 0, st>>>(in, out, nullptr, n);
+        k_scan_blocks<Tin, T><<<1, SCAN_TPB, 0, st>>>(in, out, nullptr, n);
         return;
     }
-    int* sums = tmp;
+    T* sums = tmp;
     count_launch();
-    k_scan_blocks<<<(unsigned)nb, SCAN_TPB, 0, st>>>(in, out, sums, n);
-    exclusive_scan(sums, sums, nb, tmp + nb, st);
+    k_scan_blocks<Tin, T><<<(unsigned)nb, SCAN_TPB, 0, st>>>(in, out, sums, n);
+    exclusive_scan_t<T, T>(sums, sums, nb, tmp + nb, st);
     count_launch();
-    k_scan_add<<<(unsigned)nb, SCAN_TPB, 0, st>>>(out, sums, n);
+    k_scan_add<T><<<(unsigned)nb, SCAN_TPB, 0, st>>>(out, sums, n);
+}
+
+void exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st) {
+    exclusive_scan_t<int, int>(in, out, n, tmp, st);
+}
+
+void exclusive_scan64(const int* in, long long* out, int64_t n, long long* tmp, cudaStream_t st) {
+    exclusive_scan_t<int, long long>(in, out, n, tmp, st);
 }
 
 size_t scan_tmp_elems(int64_t n) {

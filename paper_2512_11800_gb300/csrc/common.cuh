@@ -116,11 +116,12 @@ struct Layout {
     size_t order;       // int32 [T] tiles in work order (longest list first)
     size_t sched;       // SCHED_BYTES: per-launch tile queues, bucket counts and cursors
     size_t npp;         // int32 [NPIX] (pixel, Gaussian) pairs per pixel
-    size_t pq_off;      // int32 [NPIX] exclusive scan of npp
+    size_t pq_off;      // int64 [NPIX] exclusive scan of npp
     size_t pq;          // float4 [qcap][N+1] saved bound queries {tau, x0, x1, j | nroot << 4}
     size_t total;
     int64_t VP, P, npix, cap;
-    int64_t qcap;       // query slots (0: queries are recomputed by the backward)
+    int64_t qcap;       // query slots (0: queries are recomputed by the backward); a pixel keeps
+                        // its queries iff all of its pairs fit (pq_off + npp <= qcap)
     int64_t n_tiles;
     int nb_sort, sort_passes, final_buf;
     int n_views;

@@ -49,11 +49,9 @@ __device__ __forceinline__ void store_moments(const Params& p, const float acc[N
 __global__ void __launch_bounds__(TPB) k_moments(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                                                  const int32_t* __restrict__ ids, const int2* __restrict__ ranges,
                                                  int64_t P, int64_t npix, StatusWords* sw,
-                                                 void* __restrict__ moments, int* __restrict__ npp, int64_t qcap) {
+                                                 void* __restrict__ moments, int* __restrict__ npp) {
     extern __shared__ float4 s_raw[];
     float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
-    if (npp && blockIdx.x == 0 && threadIdx.x == 0 && sw->n_pixpairs > (unsigned long long)qcap)
-        set_status(&sw->status, MB3DGS_ERR_CAPACITY);
     const bool any = sw->n_valid != 0;
     int fp, fx0, fy0;
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
@@ -172,14 +170,14 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                                                const float* __restrict__ recon, const void* __restrict__ moments,
                                                float* __restrict__ rgb,
                                                float* __restrict__ T_final, float* __restrict__ penalty,
-                                               float* __restrict__ saved, const int* __restrict__ pq_off,
-                                               float4* __restrict__ pq, int64_t qcap) {
+                                               float* __restrict__ saved, const int* __restrict__ npp,
+                                               const long long* __restrict__ pq_off, float4* __restrict__ pq,
+                                               int64_t qcap) {
     extern __shared__ float4 s_raw[];
     float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
     const bool any = sw->n_valid != 0;
-    // saved queries: a pixel's pairs from pq_off[pix], N+1 float4 each; only
-    // when the frame's pixel pairs fit (so the int32 offsets cannot overflow)
-    const bool save = SAVE && sw->n_pixpairs <= (unsigned long long)qcap;
+    // saved queries: a pixel's pairs from pq_off[pix], N+1 float4 each, for
+    // the pixels all of whose pairs fit the capacity (a prefix in pixel order)
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
     int fp, fx0, fy0;
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
@@ -190,7 +188,11 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
         else R.m0 = 0.0f;
         float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, O = 0.0f, Pen = 0.0f;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-        float4* qp = (save && c.inside) ? pq + (size_t)pq_off[c.pix] * nq : nullptr;
+        float4* qp = nullptr;
+        if (SAVE && c.inside) {
+            const long long off = pq_off[c.pix];
+            if (off + npp[c.pix] <= qcap) qp = pq + (size_t)off * nq;
+        }
         for (int pos = c.start; pos < c.end; pos += 32) {
             const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
             if (c.inside) {
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
 }
 
 // ---------------------------------------------------------------- launchers
-void exclusive_scan(const int* in, int* out, int64_t n, int* tmp, cudaStream_t st);
+void exclusive_scan64(const int* in, long long* out, int64_t n, long long* tmp, cudaStream_t st);
 
 void launch_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
     if (L.n_tiles == 0) return;
@@ -237,8 +239,10 @@ void launch_moments(const Params& p, const ViewTable& vt, const Layout& L, char*
     k_moments<<<tl.grid, TPB, smem, st>>>(
         p, vt, tl.ts, reinterpret_cast<const float*>(ws + L.rec),
         reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
-        L.npix, reinterpret_cast<StatusWords*>(ws + L.status), ws + L.moments, npp, L.qcap);
-    if (npp) exclusive_scan(npp, reinterpret_cast<int*>(ws + L.pq_off), L.npix, reinterpret_cast<int*>(ws + L.scan_tmp), st);
+        L.npix, reinterpret_cast<StatusWords*>(ws + L.status), ws + L.moments, npp);
+    if (npp)
+        exclusive_scan64(npp, reinterpret_cast<long long*>(ws + L.pq_off), L.npix,
+                         reinterpret_cast<long long*>(ws + L.scan_tmp), st);
 }
 
 void launch_moments_to_power(const Params& p, const Layout& L, char* ws, float* out, cudaStream_t st) {
@@ -273,7 +277,8 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
         reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
         L.npix, reinterpret_cast<const StatusWords*>(ws + L.status), reinterpret_cast<const float*>(ws + L.recon),
         ws + L.moments, rgb, T_final, penalty, reinterpret_cast<float*>(ws + L.saved),
-        save ? reinterpret_cast<const int*>(ws + L.pq_off) : nullptr,
+        save ? reinterpret_cast<const int*>(ws + L.npp) : nullptr,
+        save ? reinterpret_cast<const long long*>(ws + L.pq_off) : nullptr,
         save ? reinterpret_cast<float4*>(ws + L.pq) : nullptr, L.qcap);
 }
 

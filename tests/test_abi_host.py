@@ -103,20 +103,29 @@ def test_execution_shape_validation_and_tile_counts(lib):
 
 
 def test_query_capacity_policy():
-    """Saved queries (16 B x (N+1) a pair) only while they fit the budget and
-    stay below 2^31 pairs; otherwise the backward recomputes them (0)."""
+    """Query slots (16 B x (N+1) a pair): all of the frame's pairs while they
+    fit the budget, else as many as the budget holds (the backward solves the
+    other pixels' queries again); none without saved queries or with the
+    trigonometric basis.  The C layout accepts capacities beyond 2^31."""
     from paper_2512_11800_gb300 import RasterConfig, Rasterizer
+    from paper_2512_11800_gb300 import _binding as B
     R = Rasterizer(RasterConfig(query_budget_gb=1.0))
     per_pair = 16 * (R.config.n_intervals + 1)
     fit = (1 << 30) // per_pair
     assert R.set_query_capacity(fit) == fit
-    assert R.set_query_capacity(fit + 1) == 0
+    assert R.set_query_capacity(fit + 1) == fit
+    assert R.set_query_capacity(10 * fit) == fit
     assert R.set_query_capacity(0) == 0
     R.config.query_budget_gb = 1e6
-    assert R.set_query_capacity(2 ** 31 - 1) == 2 ** 31 - 1
-    assert R.set_query_capacity(2 ** 31) == 0
+    assert R.set_query_capacity(2 ** 33) == 2 ** 33
+    n = C.c_size_t(0)
+    cam = _cam(128, 128)
+    assert R.lib.mb3dgs_workspace_size(C.byref(R.cfg_c), C.byref(cam), 1, 100, 0, C.byref(n)) == 0
+    assert n.value >= 2 ** 33 * per_pair
     R.config.save_queries = False
     assert R.set_query_capacity(1000) == 0
+    Rt = Rasterizer(RasterConfig(basis="trig"))
+    assert Rt.set_query_capacity(1000) == 0
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
