@@ -67,17 +67,17 @@ def alg_ops(kernel, n_intervals):
             "k_moments": moments, "k_bwd_moments": (2 * moments[0], 2 * moments[1])}[kernel]
 
 
-# Executed work of the current kernels from one ncu capture each on the
-# 200k/720p workload (per pixel pair): FP32 flops = FADD + FMUL + 2 FFMA
-# thread instructions, all thread instructions, and DRAM bytes (read +
-# write; the saved bound queries dominate).  Scaled to a launch by its pairs.
+# Executed work of the current kernels from ncu captures on the 200k/720p
+# workload (per pixel pair): FP32 flops = FADD + FMUL + 2 FFMA thread
+# instructions, all thread instructions, and DRAM bytes (read + write; the
+# kept bound queries dominate).  Scaled to a launch by its pairs.
 EXECUTED_PER_PAIR = {
-    "k_shade": dict(flops=1160.3, thread_inst=1764.4, dram_bytes=71.6),
-    "k_bwd_quadrature": dict(flops=1201.4, thread_inst=1602.7, dram_bytes=70.6),
+    "k_shade": dict(flops=1160.3, thread_inst=1478.0, dram_bytes=73.9),
+    "k_bwd_quadrature": dict(flops=1201.4, thread_inst=1582.6, dram_bytes=70.5),
 }
-# MUFU (XU) pipe utilisation of the same captures (ncu sm__inst_executed_pipe_xu
-# as a fraction of its peak), or None before it was captured.
-XU_PIPE_FRAC = {"k_shade": None, "k_bwd_quadrature": None}
+# MUFU (XU) pipe utilisation of the same captures (ncu
+# sm__inst_executed_pipe_xu.avg.pct_of_peak_sustained_active / 100).
+XU_PIPE_FRAC = {"k_shade": 0.094, "k_bwd_quadrature": 0.056}
 
 
 def measured_peaks():
