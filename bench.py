@@ -333,11 +333,12 @@ def run_single(args, dist, rank, world, dev):
     from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
     sc, cam = scenes.workload(args.workload)
     npix = cam.width * cam.height
-    R = Rasterizer(RasterConfig(basis=args.basis, n_intervals=args.n_intervals, moment_dtype=args.moment_dtype),
-                   device=dev)
+    R = Rasterizer(RasterConfig(basis=args.basis, n_intervals=args.n_intervals, moment_dtype=args.moment_dtype,
+                                tau_table=args.tau_table), device=dev)
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
-    with_bwd = not args.forward_only and args.basis == "power"   # the trigonometric basis is forward only
+    # the trigonometric basis and the tabulated transmittance are forward only
+    with_bwd = not args.forward_only and args.basis == "power" and not args.tau_table
     fr = Frame(R, g, cam, target, save_queries=with_bwd)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -415,6 +416,7 @@ def run_single(args, dist, rank, world, dev):
         config={"workload": args.workload, "gaussians": g.P, "width": cam.width, "height": cam.height,
                 "sh_degree": sc.sh_degree,
                 "n_moments": 9, "n_intervals": n_int, "basis": args.basis, "moment_storage": args.moment_dtype,
+                "tau_table_knots": args.tau_table,
                 "pass": "forward+backward (L2 loss vs random target)" if with_bwd else "forward",
                 "saved_queries": fr.qcap > 0,
                 "tiling": dict(tile=[R.config.tile_w, R.config.tile_h], batch=R.config.batch,
@@ -425,9 +427,9 @@ def run_single(args, dist, rank, world, dev):
         stage_ms=stage_ms,
         pairs=pairs, tile_pairs=tile_pairs, status=st,
         roofline=roofline(dominant, dom_ms, pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0)
-        if args.basis == "power" else None,
+        if args.basis == "power" and not args.tau_table else None,
         roofline_shade=roofline("k_shade", stage_ms["shade"], pairs, n_int, peaks, sm_mhz, captured=fr.qcap > 0)
-        if args.basis == "power" else None,
+        if args.basis == "power" and not args.tau_table else None,
         alu_peaks=peaks,
         e2e=dict(value=world * npix / (e2e_ms * 1e-3) / 1e6, unit="Mpixel/s", h2d_bytes_per_step=h2d,
                  d2h_bytes_per_step=d2h),
@@ -606,6 +608,8 @@ def main():
     ap.add_argument("--basis", default="power", choices=["power", "trig"],
                     help="moment basis; trig (Eq. 13-14) is forward only and reports no roofline")
     ap.add_argument("--n-intervals", type=int, default=3)
+    ap.add_argument("--tau-table", type=int, default=0,
+                    help="tabulated transmittance with this many knots a segment (forward only; 0: off)")
     ap.add_argument("--moment-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="storage of the per-pixel moments (accumulation is FP32 in every case)")
     args = ap.parse_args()

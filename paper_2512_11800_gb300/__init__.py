@@ -52,6 +52,8 @@ class RasterConfig:
     # moment basis: "power" (Eq. 10-12) or "trig" (Eq. 13-14, forward only)
     basis: str = "power"
     trig_theta: float = 0.5 * np.pi   # wrapping angle of the trigonometric moments
+    # tabulated transmittance (forward only): M knots a segment, 0 = solve every query
+    tau_table: int = 0
 
     def to_c(self) -> B.Config:
         c = B.Config()
@@ -64,6 +66,7 @@ class RasterConfig:
         c.schedule = B.SCHEDULES[self.schedule]
         c.basis = B.BASES[self.basis]
         c.trig_theta = float(self.trig_theta)
+        c.tau_table = int(self.tau_table)
         return c
 
 
@@ -227,7 +230,7 @@ class Rasterizer:
         n = int(n)
         per_pair = 16 * (self.config.n_intervals + 1)
         budget = int(self.config.query_budget_gb * 2 ** 30) // per_pair
-        keep = self.config.save_queries and self.config.basis == "power"   # trig: forward only
+        keep = self.config.save_queries and self.config.basis == "power" and not self.config.tau_table
         self.cfg_c.query_capacity = min(n, budget) if keep else 0
         return int(self.cfg_c.query_capacity)
 

@@ -15,7 +15,8 @@ class Config(C.Structure):
                 ("eps", C.c_float), ("bias_alpha", C.c_float), ("m_min", C.c_float), ("r_mult", C.c_float),
                 ("bg", c_float3), ("moment_dtype", C.c_int), ("strict", C.c_int),
                 ("tile_w", C.c_int), ("tile_h", C.c_int), ("batch", C.c_int), ("schedule", C.c_int),
-                ("query_capacity", C.c_int64), ("basis", C.c_int), ("trig_theta", C.c_float)]
+                ("query_capacity", C.c_int64), ("basis", C.c_int), ("trig_theta", C.c_float),
+                ("tau_table", C.c_int)]
 
 
 class Gaussians(C.Structure):

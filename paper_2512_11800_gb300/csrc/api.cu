@@ -58,6 +58,8 @@ static int check_cfg(const mb3dgs_config* c) {
     if (c->basis != MB3DGS_BASIS_POWER && c->basis != MB3DGS_BASIS_TRIG) return MB3DGS_ERR_INVALID_ARG;
     if (c->basis == MB3DGS_BASIS_TRIG && !(c->trig_theta > 0.0f && c->trig_theta < (float)(2.0 * M_PI)))
         return MB3DGS_ERR_INVALID_ARG;
+    if (c->tau_table != 0 && (c->tau_table < 8 || c->tau_table > 128)) return MB3DGS_ERR_INVALID_ARG;
+    if (c->tau_table != 0 && c->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;
     if (c->tile_w != 0 || c->tile_h != 0) {
         const int tw = c->tile_w, th = c->tile_h;
         if (!(tw == 8 || tw == 16 || tw == 32 || tw == 64) || tw * th != TPB) return MB3DGS_ERR_UNSUPPORTED;
@@ -149,6 +151,11 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     L.saved = take(sizeof(float) * 4 * (size_t)npix);
     L.dm = take(sizeof(float) * NMOM * (size_t)npix);
     L.grec = take(sizeof(float) * 28 * (size_t)L.VP);
+    L.tab_m = cfg && cfg->basis == MB3DGS_BASIS_POWER ? cfg->tau_table : 0;
+    if (L.tab_m > 0) {
+        L.tab_e = take(sizeof(float) * 4 * (size_t)npix);
+        L.tab = take(sizeof(float) * 2 * TAB_SEGS * (size_t)(L.tab_m + 1) * (size_t)npix);
+    }
     if (L.qcap > 0) {
         L.npp = take(sizeof(int) * (size_t)npix);
         L.pq_off = take(sizeof(long long) * (size_t)npix);
@@ -219,6 +226,7 @@ static void make_params(const mb3dgs_config* c, Params& p) {
     p.strict = c->strict;
     p.moment_dtype = c->moment_dtype;
     p.basis = c->basis;
+    p.tab_m = c->basis == MB3DGS_BASIS_POWER ? c->tau_table : 0;
     if (c->basis == MB3DGS_BASIS_TRIG) {
         const double A = 2.0 * M_PI - (double)c->trig_theta;
         p.trig_A = (float)A;
@@ -423,6 +431,7 @@ int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* ca
                                int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
                                const float* d_dL_dpenalty, const float* d_dL_dT, mb3dgs_stream_t stream) {
     if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
+    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
@@ -435,6 +444,7 @@ int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* ca
 int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                             int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream) {
     if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
+    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
@@ -446,6 +456,7 @@ int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians*
                                int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity,
                                const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
     if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
+    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     int rc = check_grads(g, grads);
     if (rc) return rc;
     Ctx c;
@@ -461,6 +472,7 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
                     const float* d_dL_dpenalty, const float* d_dL_dT, const mb3dgs_gaussian_grads* grads,
                     mb3dgs_stream_t stream) {
     if (cfg && cfg->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // adjoint: power basis only
+    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     int rc = check_grads(g, grads);
     if (rc) return rc;
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;

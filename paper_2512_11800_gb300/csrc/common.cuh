@@ -23,6 +23,7 @@ constexpr int MAX_NODES = 9;          // N+1 <= 9 sample points
 constexpr int LAG_ITERS = 4;          // Laguerre iterations per root
 constexpr int SCHED_BYTES = 512;      // tile-queue counters and order buckets
 constexpr double OUTER_SPAN = 8.0;   // outer-root search span beyond the Gauss nodes (y units)
+constexpr int TAB_SEGS = 5;           // segments of the tabulated transmittance (between Gauss nodes)
 
 // record field offsets (floats)
 enum RecField {
@@ -84,6 +85,7 @@ struct Params {
     float trig_A;          // angle range 2 pi - theta of the trigonometric moments
     float trig_lo;         // cut -theta/2 (middle of the wrapping zone)
     float cstar_re[4], cstar_im[4];   // moments of the uniform distribution on [0, A] (bias target)
+    int tab_m;             // knots per segment of the tabulated transmittance (0: off)
 };
 
 // Workspace layout (byte offsets), computed on the host.
@@ -118,6 +120,9 @@ struct Layout {
     size_t npp;         // int32 [NPIX] (pixel, Gaussian) pairs per pixel
     size_t pq_off;      // int64 [NPIX] exclusive scan of npp
     size_t pq;          // float4 [qcap][N+1] saved bound queries {tau, x0, x1, j | nroot << 4}
+    size_t tab_e;       // float [4][NPIX] segment edges of the tabulated transmittance
+    size_t tab;         // float2 [5 (M+1)][NPIX] tabulated (tau, dtau/deta)
+    int tab_m;          // knots per segment M (0: no table)
     size_t total;
     int64_t VP, P, npix, cap;
     int64_t qcap;       // query slots (0: queries are recomputed by the backward); a pixel keeps

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "table.cuh"
 #include "tile.cuh"
 
 namespace mb {
@@ -151,13 +152,48 @@ __global__ void k_reconstruct(Params p, const void* __restrict__ moments, int64_
     }
 }
 
+// Per-pixel table of the tabulated transmittance (table.cuh): segment edges
+// and M + 1 knots a segment, one thread per pixel.
+__global__ void k_build_table(Params p, int64_t npix, const float* __restrict__ recon, float* __restrict__ tab_e,
+                              float2* __restrict__ tab) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= npix) return;
+    const Recon R = load_recon(recon, npix, pix);
+    float e[4];
+    table_edges(R, e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tab_e[k * npix + pix] = e[k];
+    const int M = p.tab_m;
+#pragma unroll 1
+    for (int s = 0; s < TAB_SEGS; ++s)
+#pragma unroll 1
+        for (int i = 0; i <= M; ++i) tab[(size_t)(s * (M + 1) + i) * npix + pix] = table_knot(p, R, e, s, i, M);
+}
+
 // ---------------------------------------------------------------- quadrature pass
-__device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, int64_t npix, int64_t pix, Recon& R) {
+struct TableArgs {
+    const float2* tab;
+    const float* tab_e;
+    int M;
+};
+
+__device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, int64_t npix, int64_t pix,
+                                                 const TableArgs&, Recon& R) {
     R = load_recon(rc, npix, pix);
 }
 __device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, int64_t npix, int64_t pix,
-                                                 TrigRecon& T) {
+                                                 const TableArgs&, TrigRecon& T) {
     T = load_trig_recon(rc, npix, pix);
+}
+__device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, int64_t npix, int64_t pix,
+                                                 const TableArgs& ta, TabPixel& T) {
+    T.m0 = rc[pix];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) T.e[k] = ta.tab_e[k * npix + pix];
+    T.tab = ta.tab;
+    T.pix = pix;
+    T.npix = npix;
+    T.M = ta.M;
 }
 
 #ifndef MB_SHADE_MIN_CTAS
@@ -172,7 +208,7 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                                                float* __restrict__ T_final, float* __restrict__ penalty,
                                                float* __restrict__ saved, const int* __restrict__ npp,
                                                const long long* __restrict__ pq_off, float4* __restrict__ pq,
-                                               int64_t qcap) {
+                                               int64_t qcap, TableArgs ta) {
     extern __shared__ float4 s_raw[];
     float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
     const bool any = sw->n_valid != 0;
@@ -184,7 +220,7 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
         PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
         RecT R;
-        if (c.inside) load_pixel_state(recon, npix, c.pix, R);
+        if (c.inside) load_pixel_state(recon, npix, c.pix, ta, R);
         else R.m0 = 0.0f;
         float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, O = 0.0f, Pen = 0.0f;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
@@ -257,6 +293,12 @@ void launch_reconstruct(const Params& p, const Layout& L, char* ws, const float*
     count_launch();
     k_reconstruct<<<(unsigned)ceil_div64(L.npix, 128), 128, 0, st>>>(
         p, ws + L.moments, L.npix, reinterpret_cast<float*>(ws + L.recon), eta, Q, T_out);
+    if (L.tab_m > 0) {
+        count_launch();
+        k_build_table<<<(unsigned)ceil_div64(L.npix, 128), 128, 0, st>>>(
+            p, L.npix, reinterpret_cast<const float*>(ws + L.recon), reinterpret_cast<float*>(ws + L.tab_e),
+            reinterpret_cast<float2*>(ws + L.tab));
+    }
 }
 
 void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* ws, float* rgb, float* T_final,
@@ -267,6 +309,9 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
     auto kern = p.basis == MB3DGS_BASIS_TRIG
                     ? (p.n_intervals == 3 ? k_shade<3, false, TrigRecon>
                        : p.n_intervals == 5 ? k_shade<5, false, TrigRecon> : k_shade<0, false, TrigRecon>)
+              : L.tab_m > 0
+                    ? (p.n_intervals == 3 ? k_shade<3, false, TabPixel>
+                       : p.n_intervals == 5 ? k_shade<5, false, TabPixel> : k_shade<0, false, TabPixel>)
               : p.n_intervals == 3 ? (save ? k_shade<3, true, Recon> : k_shade<3, false, Recon>)
               : p.n_intervals == 5 ? (save ? k_shade<5, true, Recon> : k_shade<5, false, Recon>)
                                    : (save ? k_shade<0, true, Recon> : k_shade<0, false, Recon>);
@@ -279,7 +324,9 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
         ws + L.moments, rgb, T_final, penalty, reinterpret_cast<float*>(ws + L.saved),
         save ? reinterpret_cast<const int*>(ws + L.npp) : nullptr,
         save ? reinterpret_cast<const long long*>(ws + L.pq_off) : nullptr,
-        save ? reinterpret_cast<float4*>(ws + L.pq) : nullptr, L.qcap);
+        save ? reinterpret_cast<float4*>(ws + L.pq) : nullptr, L.qcap,
+        TableArgs{L.tab_m > 0 ? reinterpret_cast<const float2*>(ws + L.tab) : nullptr,
+                  L.tab_m > 0 ? reinterpret_cast<const float*>(ws + L.tab_e) : nullptr, L.tab_m});
 }
 
 }  // namespace mb

@@ -13,12 +13,14 @@
 // warped depths eta_q = q/16), argv[3] (optional) = N intervals (default 3;
 // other values run the runtime-N template), argv[4] (optional) = moment basis
 // (0 power, 1 trigonometric: trig_moments, reconstruct_trig and the
-// trigonometric bound queries).
+// trigonometric bound queries), argv[5] (optional) = knots M of the tabulated
+// transmittance (power basis; 0: every query solved).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
 #include "../../paper_2512_11800_gb300/csrc/preprocess.cuh"
 #include "../../paper_2512_11800_gb300/csrc/api.cu"
+#include "../../paper_2512_11800_gb300/csrc/table.cuh"
 
 namespace mb {   // the launchers api.cu refers to; never called here
 void launch_preprocess(const Params&, const ViewTable&, const mb3dgs_gaussians&, float*, int*, StatusWords*,
@@ -47,7 +49,7 @@ static void rd(FILE* f, T* x, size_t n) {
 }
 
 int main(int argc, char** argv) {
-    if (argc < 3 || argc > 5) return 2;
+    if (argc < 3 || argc > 6) return 2;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
     int64_t P;
@@ -70,6 +72,7 @@ int main(int argc, char** argv) {
     mb3dgs_config_default(&cfg);
     if (argc >= 4) cfg.n_intervals = atoi(argv[3]);
     if (argc >= 5) cfg.basis = atoi(argv[4]);
+    if (argc >= 6) cfg.tau_table = atoi(argv[5]);
     const bool trig = cfg.basis == MB3DGS_BASIS_TRIG;
     Params p;
     make_params(&cfg, p);
@@ -106,6 +109,20 @@ int main(int argc, char** argv) {
         TrigRecon TR;
         if (trig) reconstruct_trig(p, acc, TR);
         else reconstruct_pixel(p, acc, R);
+        // tabulated transmittance: this pixel's table (npix = 1 layout)
+        const int M = p.tab_m;
+        std::vector<float2> tab(M > 0 ? TAB_SEGS * (M + 1) : 1);
+        TabPixel TP;
+        if (M > 0) {
+            table_edges(R, TP.e);
+            for (int s = 0; s < TAB_SEGS; ++s)
+                for (int i = 0; i <= M; ++i) tab[s * (M + 1) + i] = table_knot(p, R, TP.e, s, i, M);
+            TP.m0 = R.m0;
+            TP.tab = tab.data();
+            TP.pix = 0;
+            TP.npix = 1;
+            TP.M = M;
+        }
         float S[3] = {0, 0, 0}, O = 0, Pen = 0;
         for (int64_t i : list) {
             const float* r = &rec[i * REC];
@@ -114,6 +131,7 @@ int main(int argc, char** argv) {
             float Oi;
             if (trig) Oi = p.n_intervals == 5 ? pair_quadrature<5, false, TrigRecon>(p, TR, g, &Pen)
                                               : pair_quadrature<0, false, TrigRecon>(p, TR, g, &Pen);
+            else if (M > 0) Oi = pair_quadrature<0, false, TabPixel>(p, TP, g, &Pen);
             else Oi = p.n_intervals == 3 ? pair_quadrature<3>(p, R, g, &Pen) : pair_quadrature<0>(p, R, g, &Pen);
             for (int c = 0; c < 3; ++c) S[c] += r[R_RGB + c] * Oi;
             O += Oi;
@@ -123,6 +141,7 @@ int main(int argc, char** argv) {
         out_T[q] = Tf;
         for (int k = 0; k < NPROBE; ++k)
             out_probe[q * NPROBE + k] = trig ? expf(-trig_optical_depth(p, TR, (float)k / 16.0f))
+                                      : M > 0 ? expf(-table_depth(TP, (float)k / 16.0f))
                                              : expf(-optical_depth(R, p.beta, 2.0f * ((float)k / 16.0f) - 1.0f));
     }
     FILE* o = fopen(argv[2], "wb");
