@@ -438,12 +438,21 @@ def run_single(args, dist, rank, world, dev):
     )
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(sc, cam, with_bwd, name=args.workload)
+    if (world == 1 and args.workload == WORKLOAD and with_bwd and args.basis == "power" and not args.tau_table
+            and args.moment_dtype == "f32" and not args.no_batch16):
+        # the many-view configuration (16 views of uneven resolution), short form
+        del fr, g2, dev_in, outbuf, grads2
+        R._ws = None
+        torch.cuda.empty_cache()
+        line["batch16"] = run_batch16(args, None, rank, world, dev, summary=True)
     return line
 
 
-def run_batch16(args, dist, rank, world, dev):
+def run_batch16(args, dist, rank, world, dev, summary=False):
     """16 views of uneven resolution: fwd+bwd in one CUDA graph vs 16 sequential
-    single-view calls (eager)."""
+    single-view calls (eager).  summary=True: the short form nested in the
+    default bench line (default execution shape instead of the autotuner, 2
+    sequential steps, no end-to-end leg); returns a dict."""
     from paper_2512_11800_gb300 import GaussianTensors, RasterConfig, Rasterizer
     sc, _ = scenes.workload(WORKLOAD)
     cams = scenes.multiview_cameras(16, seed=4, radius=3.0, fov_deg=60.0)
@@ -452,7 +461,8 @@ def run_batch16(args, dist, rank, world, dev):
     R = Rasterizer(RasterConfig(), device=dev)
     # execution shape tuned on the largest view (fwd+bwd), shared by all views
     big = max(range(len(cams)), key=lambda i: npix[i])
-    tuned = R.autotune(g, cams[big], backward=True)
+    c0 = R.config
+    tuned = (c0.tile_w, c0.tile_h, c0.batch, c0.schedule, None) if summary else R.autotune(g, cams[big], backward=True)
     rng = np.random.default_rng(12)
     target = torch.as_tensor(rng.random((sum(npix), 3), dtype=np.float32), device=dev)
     stream = torch.cuda.current_stream()
@@ -473,16 +483,17 @@ def run_batch16(args, dist, rank, world, dev):
         for f in frames:
             f.step(stream, with_bwd)
 
-    for _ in range(args.warmup):
+    seq_warm, seq_steps = (1, 2) if summary else (args.warmup, args.steps)
+    for _ in range(seq_warm):
         seq_step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(seq_steps):
         seq_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    seq_ms = e0.elapsed_time(e1) / args.steps
+    seq_ms = e0.elapsed_time(e1) / seq_steps
     del frames, shared
     R._ws = None
     torch.cuda.empty_cache()
@@ -541,6 +552,14 @@ def run_batch16(args, dist, rank, world, dev):
     st = max((pair_counts(R, f)[0] for f in fbs), key=abs)
     tile_pairs = sum(c[0] for c in counts)
     pairs = sum(c[1] for c in counts)
+    if summary:
+        tot = sum(npix)
+        return dict(workload="batch16_shells1M: 16 views (640x360 / 1280x720 / 1920x1080), one frame in one CUDA "
+                             "graph, forward + backward",
+                    value=world * tot / (ms * 1e-3) / 1e6, unit="Mpixel/s", ms_per_step=ms, steps=args.steps,
+                    sequential_ms_per_step=seq_ms, sequential_mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
+                    speedup_vs_sequential=seq_ms / ms, pixels=tot, pixel_pairs=pairs,
+                    kept_queries_frac=fbs[0].qcap / max(pp, 1), gpu_launches=int(launches), status=st, clocks=clk)
 
     # end to end: inputs from pinned host memory into the graph's input
     # buffers, replay, rgb back to host
@@ -604,6 +623,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.WORKLOADS) + ["batch16"],
                     help="the default is the headline workload; the others are for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch16", action="store_true",
+                    help="leave out the short 16-view record the default workload adds to its line")
     ap.add_argument("--forward-only", action="store_true")
     ap.add_argument("--basis", default="power", choices=["power", "trig"],
                     help="moment basis; trig (Eq. 13-14) is forward only and reports no roofline")

@@ -349,7 +349,7 @@ MB_HD float laguerre_step(float x, float f, float fp, float fpp, float lo, float
 // which sets the accuracy of the root.
 MB_HD float laguerre(const Recon& R, const float e[5], const float c[5], float x, float lo, float hi,
                      bool right) {
-#pragma unroll 1
+#pragma unroll
     for (int it = 0; it < LAG_ITERS - 1; ++it) {
         float f = c[4], d1 = 0.0f, d2 = 0.0f;
 #pragma unroll
