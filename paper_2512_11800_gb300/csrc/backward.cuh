@@ -254,7 +254,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
     }
     load_sample<SAVED>(p, R, g, isq, 0, qa, c);
     // T_j = e^{-tau_j}, carried: T_{j+1} = T_j e^{-dtau_j} (e^{-dtau} = 1 - dtau ph)
-    float Tc = expf(-c.tau), Tn = Tc;
+    float Tc = exp_(-c.tau), Tn = Tc;
 #pragma unroll 1
     for (int j = 0; j <= N; ++j) {
         if (j < N) {
@@ -278,10 +278,11 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
                 dph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, -1.0f / 144.0f, 1.0f / 30.0f), -0.125f), 1.0f / 3.0f),
                            -0.5f);
             } else {
-                const float xm = expm1f(-dtau);   // e^-x - 1
+                // dtau >= 0.05: 1 - e^-x keeps its digits with the fast exponential
+                const float em = exp_(-dtau);
                 const float idt = fdiv_(1.0f, dtau);
-                ph = -xm * idt;
-                dph = (1.0f + xm - ph) * idt;
+                ph = (1.0f - em) * idt;
+                dph = (em - ph) * idt;
             }
             Tn = Tj * fmaf(-dtau, ph, 1.0f);
             const float term = Tj * ph * sig * Delta;
