@@ -156,11 +156,11 @@ def job_mpix_s(world, pixels_per_rank, ms):
     return world * pixels_per_rank / (ms * 1e-3) / 1e6
 
 
-def oracle_step(sc, cam, size, with_bwd, target):
+def oracle_step(sc, cam, size, with_bwd, target, basis="power", n_intervals=3):
     """One oracle step on a centred size x size crop: forward, or forward +
     gradient of the L2 loss against the target crop (autograd in FP64)."""
     import oracle as O
-    cfg = O.OracleConfig()
+    cfg = O.OracleConfig(basis=basis, n_intervals=n_intervals)
     x0, y0 = (cam.width - size) // 2, (cam.height - size) // 2
     region = (x0, y0, size, size)
     if not with_bwd:
@@ -172,12 +172,12 @@ def oracle_step(sc, cam, size, with_bwd, target):
     return O.render_grad(sc, cam, cfg, g, None, region=region)["out"]["n_pairs"]
 
 
-def cpu_oracle_sample(sc, cam, with_bwd, size=32, name=WORKLOAD):
+def cpu_oracle_sample(sc, cam, with_bwd, size=32, name=WORKLOAD, basis="power", n_intervals=3):
     """Time the FP64 oracle on a centred crop of the same workload (bounded sample)."""
     torch.set_num_threads(os.cpu_count() or 1)
     target = scenes.target_image(cam.height, cam.width)
     t0 = time.perf_counter()
-    n_pairs = oracle_step(sc, cam, size, with_bwd, target)
+    n_pairs = oracle_step(sc, cam, size, with_bwd, target, basis, n_intervals)
     dt = time.perf_counter() - t0
     return dict(value=size * size / dt / 1e6, unit="Mpixel/s", cores=torch.get_num_threads(), kind="oracle",
                 sample="centre %dx%d crop of the %dx%d frame of %s (%d pixel pairs), %s, %.1f s" %
@@ -337,8 +337,8 @@ def run_single(args, dist, rank, world, dev):
                                 tau_table=args.tau_table), device=dev)
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
-    # the trigonometric basis and the tabulated transmittance are forward only
-    with_bwd = not args.forward_only and args.basis == "power" and not args.tau_table
+    # the tabulated transmittance is forward only
+    with_bwd = not args.forward_only and not args.tau_table
     fr = Frame(R, g, cam, target, save_queries=with_bwd)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -437,7 +437,8 @@ def run_single(args, dist, rank, world, dev):
         clocks=clk,
     )
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(sc, cam, with_bwd, name=args.workload)
+        line["cpu_baseline"] = cpu_oracle_sample(sc, cam, with_bwd, name=args.workload, basis=args.basis,
+                                                 n_intervals=n_int)
     if (world == 1 and args.workload == WORKLOAD and with_bwd and args.basis == "power" and not args.tau_table
             and args.moment_dtype == "f32" and not args.no_batch16):
         # the many-view configuration (16 views of uneven resolution), short form
@@ -627,7 +628,7 @@ def main():
                     help="leave out the short 16-view record the default workload adds to its line")
     ap.add_argument("--forward-only", action="store_true")
     ap.add_argument("--basis", default="power", choices=["power", "trig"],
-                    help="moment basis; trig (Eq. 13-14) is forward only and reports no roofline")
+                    help="moment basis; trig (Eq. 13-14) reports no roofline (its node solve has no fixed op count)")
     ap.add_argument("--n-intervals", type=int, default=3)
     ap.add_argument("--tau-table", type=int, default=0,
                     help="tabulated transmittance with this many knots a segment (forward only; 0: off)")

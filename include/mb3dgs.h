@@ -60,8 +60,9 @@ enum { MB3DGS_MOMENTS_F32 = 0, MB3DGS_MOMENTS_BF16 = 1, MB3DGS_MOMENTS_F16 = 2 }
 /* Moment basis.  POWER: power moments of the warped depth (Sec. 3.2,
  * Eq. 10-12) with the bounds of Eq. 8.  TRIG: trigonometric moments (Sec. 3.2,
  * Eq. 13-14; App. C) of the angle (2 pi - theta) g-hat, with the bounds of the
- * Gauss-Szego rule on the unit circle cut in the middle of the wrapping zone
- * (forward only: the adjoint calls return MB3DGS_ERR_UNSUPPORTED). */
+ * Gauss-Szego rule on the unit circle cut in the middle of the wrapping zone.
+ * Both bases have the adjoint calls (the TRIG adjoint solves its bound
+ * queries again in pass 1: query_capacity is ignored). */
 enum { MB3DGS_BASIS_POWER = 0, MB3DGS_BASIS_TRIG = 1 };
 /* How the per-tile passes map tiles of all views to CTAs.  QUEUE: one wave of
  * persistent CTAs takes tiles from an atomic queue in decreasing order of
@@ -234,9 +235,12 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
  *   quadrature, penalty and bound queries (saved by mb3dgs_shade when
  *   cfg->query_capacity > 0, else solved again); direct derivatives go to
  *   per-record gradients in the workspace (zeroed first), the bound
- *   derivatives to the per-pixel moment adjoint.
+ *   derivatives to the per-pixel moment adjoint (TRIG: through the
+ *   Verblunsky coefficients and reverse-mode Levinson-Durbin to the raw
+ *   trigonometric moments).
  * backward_moments (pass 2): per pair the moment adjoint through the reverse
- *   sweep of the moment recurrence (Eq. 10-12) into the record gradients.
+ *   sweep of the moment recurrence (Eq. 10-12; TRIG: of Eq. 14) into the
+ *   record gradients.
  * backward_preprocess: chain rule through stage 1 to the Gaussian parameters
  *   (every entry of *grads is written). */
 int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,

@@ -49,7 +49,7 @@ class RasterConfig:
     tile_h: int = 16
     batch: int = 256
     schedule: str = "queue"        # "queue" | "grid"
-    # moment basis: "power" (Eq. 10-12) or "trig" (Eq. 13-14, forward only)
+    # moment basis: "power" (Eq. 10-12) or "trig" (Eq. 13-14)
     basis: str = "power"
     trig_theta: float = 0.5 * np.pi   # wrapping angle of the trigonometric moments
     # tabulated transmittance (forward only): M knots a segment, 0 = solve every query

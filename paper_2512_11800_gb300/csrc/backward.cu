@@ -7,6 +7,7 @@
 // (tile, record, field) in pass 2.  Work comes from the schedule of tile.cuh
 // like the forward passes.
 #include "backward.cuh"
+#include "moments.cuh"
 #include "preprocess.cuh"
 #include "tile.cuh"
 
@@ -35,17 +36,38 @@ __device__ __forceinline__ void flush_chunk(const float* s_buf, const float* s_s
     }
 }
 
+// Per-pixel bound state of the adjoint passes and the pixel's moment adjoint
+// from its summed query adjoints.
+__device__ __forceinline__ void load_bound(const float* __restrict__ recon, int64_t npix, int64_t pix, Recon& R) {
+    R = load_recon(recon, npix, pix);
+}
+__device__ __forceinline__ void load_bound(const float* __restrict__ recon, int64_t npix, int64_t pix, TrigRecon& T) {
+    T = load_trig_recon(recon, npix, pix);
+}
+__device__ __forceinline__ void finish_pixel(const Params& p, const Recon& R, const float B[NB], float gm0,
+                                             const void*, int64_t, int64_t, float psi[NPOLY]) {
+    phi_monomials(R, B, psi);
+    finish_moment_adjoint(p, R, gm0, psi);
+}
+__device__ __forceinline__ void finish_pixel(const Params& p, const TrigRecon&, const float A[NTRIG_ADJ], float gm0,
+                                             const void* moments, int64_t npix, int64_t pix, float psi[NPOLY]) {
+    float I[NMOM];
+    load_moments(p, moments, npix, pix, I);
+    trig_finish_adjoint(p, I, A, gm0, psi);
+}
+
 // ---------------------------------------------------------------- pass 1
 // Per pair: the quadrature, penalty and bound-query adjoint.  The direct
 // derivatives go through the record geometry to the per-record gradients;
-// the bound derivatives sum into the pixel's Phi, written out as the moment
-// adjoint polynomial psi.  Warp-level units as in the forward passes: each
+// the bound derivatives sum per pixel (power moments: the polynomial Phi;
+// trigonometric moments: the Verblunsky-coefficient adjoints), written out
+// as the pixel's moment adjoint psi.  Warp-level units as in the forward passes: each
 // warp walks its footprint's records, reduces every record's compact sums
 // over its 32 pixels and adds them to the record gradients per chunk.
 // SAVED: only the pixels whose bound queries the quadrature pass kept
 // (pq_off + npp <= qcap), read instead of solved; otherwise the pixels that
 // kept none (all pixels when qcap == 0), whose queries are solved again.
-template <int NI, bool SAVED>
+template <int NI, bool SAVED, class RecT>
 __global__ void __launch_bounds__(TPB, 2)
     k_bwd_quadrature(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                      const int32_t* __restrict__ ids, const int2* __restrict__ ranges, int64_t P, int64_t npix,
@@ -71,13 +93,14 @@ __global__ void __launch_bounds__(TPB, 2)
         }
         if (!any || !__any_sync(0xffffffffu, c.inside)) c.end = c.start;
         const float4* qp = nullptr;
-        Recon R;
+        RecT R;
         PixelAdj pa;
-        float B[NB];
+        constexpr int NACC = BoundAdj<RecT>::NACC;
+        float B[NACC];
 #pragma unroll
-        for (int k = 0; k < NB; ++k) B[k] = 0.0f;
+        for (int k = 0; k < NACC; ++k) B[k] = 0.0f;
         if (c.inside) {
-            R = load_recon(recon, npix, c.pix);
+            load_bound(recon, npix, c.pix, R);
             const float S[3] = {saved[c.pix], saved[npix + c.pix], saved[2 * npix + c.pix]};
             const float O = saved[3 * npix + c.pix];
             const float g[3] = {dL_drgb[3 * c.pix], dL_drgb[3 * c.pix + 1], dL_drgb[3 * c.pix + 2]};
@@ -107,7 +130,7 @@ __global__ void __launch_bounds__(TPB, 2)
                     const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
                     const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
                     const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
-                    const PairOut po = pair_backward<NI, SAVED>(p, R, g, a, pa.gP, B, qp);
+                    const PairOut po = pair_backward<NI, SAVED, RecT>(p, R, g, a, pa.gP, B, qp);
                     if (SAVED) qp += nq;
                     geometry_adjoint_compact(r, dx, dy, c.rlen, g, po.g_mu, po.g_Sig, po.g_what, acc);
                     acc[K_RGB + 0] = pa.gS[0] * po.O;
@@ -122,8 +145,7 @@ __global__ void __launch_bounds__(TPB, 2)
         }
         if (c.inside) {
             float psi[NPOLY];
-            phi_monomials(R, B, psi);
-            finish_moment_adjoint(p, R, pa.gm0, psi);
+            finish_pixel(p, R, B, pa.gm0, moments, npix, c.pix, psi);
 #pragma unroll
             for (int k = 0; k < NPOLY; ++k) psi_out[k * npix + c.pix] = psi[k];
         }
@@ -144,7 +166,8 @@ __device__ __forceinline__ void flush_batch(const float* s_rec, const float* s_a
 
 // ---------------------------------------------------------------- pass 2
 // Per pair: int psi d(d mu_i) through the reverse sweep of the moment
-// recurrence, chained to the record geometry (fields before G_RGB).  One CTA
+// recurrence (TRIG: the reverse of the trigonometric moments), chained to the
+// record geometry (fields before G_RGB).  One CTA
 // works on one tile at a time with record batches staged for the whole CTA:
 // its per-record sums are combined over the tile's 256 pixels in shared
 // memory before the global atomics (one per tile, record and field), which
@@ -152,6 +175,7 @@ __device__ __forceinline__ void flush_batch(const float* s_rec, const float* s_a
 #ifndef MB_BWD_MOMENTS_MIN_CTAS
 #define MB_BWD_MOMENTS_MIN_CTAS 4
 #endif
+template <bool TRIG>
 __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
     k_bwd_moments(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec, const int32_t* __restrict__ ids,
                   const int2* __restrict__ ranges, int64_t P, int64_t npix, const StatusWords* sw,
@@ -168,8 +192,10 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
         Recon R;                                      // only the standardisation (c, 1/s) is used
         float psi[NPOLY];
         if (c.inside) {
-            R.c = recon[1 * npix + c.pix];
-            R.inv_s = recon[2 * npix + c.pix];
+            if (!TRIG) {
+                R.c = recon[1 * npix + c.pix];
+                R.inv_s = recon[2 * npix + c.pix];
+            }
 #pragma unroll
             for (int k = 0; k < NPOLY; ++k) psi[k] = psi_in[k * npix + c.pix];
         }
@@ -189,7 +215,8 @@ __global__ void __launch_bounds__(TPB, MB_BWD_MOMENTS_MIN_CTAS)
                     const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
                     const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
                     float g_mu = 0.0f, g_Sig = 0.0f, g_what = 0.0f;
-                    moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
+                    if (TRIG) trig_moment_adjoint(p, g, psi, &g_mu, &g_Sig, &g_what);
+                    else moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
                     geometry_adjoint_compact(r, dx, dy, c.rlen, g, g_mu, g_Sig, g_what, acc);
                 }
                 const float v = reduce_scatter16(acc);
@@ -381,8 +408,12 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
     // the rest (those beyond the capacity; the launch exits early when none)
     for (int pass = kept ? 0 : 1; pass < 2; ++pass) {
         const bool saved_q = pass == 0;
-        auto k1 = p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true> : k_bwd_quadrature<3, false>)
-                                     : (saved_q ? k_bwd_quadrature<0, true> : k_bwd_quadrature<0, false>);
+        auto k1 = p.basis == MB3DGS_BASIS_TRIG
+                      ? (p.n_intervals == 3   ? k_bwd_quadrature<3, false, TrigRecon>
+                         : p.n_intervals == 5 ? k_bwd_quadrature<5, false, TrigRecon>
+                                              : k_bwd_quadrature<0, false, TrigRecon>)
+                  : p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true, Recon> : k_bwd_quadrature<3, false, Recon>)
+                                       : (saved_q ? k_bwd_quadrature<0, true, Recon> : k_bwd_quadrature<0, false, Recon>);
         if (!allow_dynamic_smem((const void*)k1, smem)) return MB3DGS_ERR_CUDA;
         const TileLaunch t1 = tile_launch(p, L, ws, Q_BWD_QUAD, (const void*)k1, smem, st);
         count_launch();
@@ -403,10 +434,11 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
 int launch_backward_moments(const Params& p, const ViewTable& vt, const Layout& L, char* ws, cudaStream_t st) {
     if (L.n_tiles == 0) return MB3DGS_OK;
     const size_t smem = sizeof(float) * (REC + NK_MOM) * p.batch;
-    if (!allow_dynamic_smem((const void*)k_bwd_moments, sizeof(float) * (REC + NK_MOM) * TPB)) return MB3DGS_ERR_CUDA;
-    const TileLaunch t2 = tile_launch(p, L, ws, Q_BWD_MOM, (const void*)k_bwd_moments, smem, st);
+    auto k2 = p.basis == MB3DGS_BASIS_TRIG ? k_bwd_moments<true> : k_bwd_moments<false>;
+    if (!allow_dynamic_smem((const void*)k2, sizeof(float) * (REC + NK_MOM) * TPB)) return MB3DGS_ERR_CUDA;
+    const TileLaunch t2 = tile_launch(p, L, ws, Q_BWD_MOM, (const void*)k2, smem, st);
     count_launch();
-    k_bwd_moments<<<t2.grid, TPB, smem, st>>>(
+    k2<<<t2.grid, TPB, smem, st>>>(
         p, vt, t2.ts, reinterpret_cast<const float*>(ws + L.rec),
         reinterpret_cast<const int32_t*>(ws + L.vals[L.final_buf]), reinterpret_cast<const int2*>(ws + L.ranges), L.P,
         L.npix, reinterpret_cast<const StatusWords*>(ws + L.status), reinterpret_cast<const float*>(ws + L.recon),

@@ -22,6 +22,7 @@
 //   dtau = int [(1-alpha) Phi + alpha int Phi dU] d(dmu)   (dmu: raw measure).
 #pragma once
 #include "common.cuh"
+#include "trig_adjoint.cuh"
 
 namespace mb {
 
@@ -192,25 +193,65 @@ struct PairOut {
 // B and returns the direct derivatives with respect to (mu, Sigma, w-hat).
 // With SAVED the bound queries come from the quadrature pass (qin, N+1 float4)
 // instead of being solved again.
+// The query record and the per-pixel adjoint size of a bound representation:
+// power moments (Phi coefficients B) or trigonometric moments (m0 and the
+// Verblunsky-coefficient adjoints).
+template <class RecT>
+struct BoundAdj;
+template <>
+struct BoundAdj<Recon> {
+    typedef QueryRec Query;
+    static constexpr int NACC = NB;
+};
+template <>
+struct BoundAdj<TrigRecon> {
+    typedef TrigQueryRec Query;
+    static constexpr int NACC = NTRIG_ADJ;
+};
+
 // One sample t_j of a pair with its bound query and running adjoints.
+template <class QR>
 struct Sample {
     float t, tau, dg, b, erf, gau;   // sample, optical depth, warp slope, b = (t - mu)/(sqrt2 Sigma), erf(b), e^{-b^2}
     bool clamped;               // t_j clamped to [t_n, t_f] (no derivative to mu, Sigma)
-    QueryRec q;
+    QR q;
     float gt, gtau;             // dL/dt_j, dL/dtau_j
 };
 
+// Optical depth of a sample at warped depth gj with its query record: read
+// from the kept query (SAVED, power moments only) or solved again.
 template <bool SAVED>
-MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float isq, int j, float4 qv, Sample& s) {
+MB_HD float sample_query(const Params& p, const Recon& R, float gj, float4 qv, QueryRec& q) {
+    if (SAVED) return unpack_query(qv, (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, q);
+    return bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q);
+}
+template <bool SAVED>
+MB_HD float sample_query(const Params& p, const TrigRecon& T, float gj, float4, TrigQueryRec& q) {
+    return trig_bound_query<true>(p, T, gj, &q);
+}
+
+// Adjoint of a sample's bound query for dL/dtau = gq: adds to the pixel's
+// accumulators and returns dL/d(warped depth).
+MB_HD float sample_query_adjoint(const Params& p, const Recon& R, const QueryRec& q, float gq, float B[NB]) {
+    float gy = 0.0f;
+    query_adjoint(p, R, q, gq, &gy, B);
+    return gy * 2.0f * R.inv_s;   // y' = (2 g-hat - 1 - c) / s
+}
+MB_HD float sample_query_adjoint(const Params& p, const TrigRecon& T, const TrigQueryRec& q, float gq,
+                                 float A[NTRIG_ADJ]) {
+    float ge = 0.0f;
+    trig_query_adjoint(p, T, q, gq, &ge, A);
+    return ge;
+}
+
+template <bool SAVED, class RecT, class QR>
+MB_HD void load_sample(const Params& p, const RecT& R, const Gauss1D& g, float isq, int j, float4 qv, Sample<QR>& s) {
     const float raw = fmaf(p.kappa * g.Sig, p.x_nodes[j], g.mu);
     s.t = fminf(fmaxf(raw, p.t_near), p.t_far);
     s.clamped = s.t != raw;
     float gj;
     warp_g(p, s.t, gj, s.dg);
-    if (SAVED)
-        s.tau = unpack_query(qv, (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, s.q);
-    else
-        s.tau = bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &s.q);
+    s.tau = sample_query<SAVED>(p, R, gj, qv, s.q);
     s.b = (s.t - g.mu) * isq;
     s.erf = p.x_erf[j];
     s.gau = p.x_gau[j];
@@ -231,8 +272,8 @@ MB_HD void load_sample(const Params& p, const Recon& R, const Gauss1D& g, float 
 // adjoints are final and go through its bound query (one copy of the query
 // code, no per-sample arrays).  Saved queries are read one sample ahead of
 // their use, so each load overlaps a whole interval's arithmetic.
-template <int NI, bool SAVED = false>
-MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, float a, float gP, float B[NB],
+template <int NI, bool SAVED = false, class RecT = Recon>
+MB_HD PairOut pair_backward(const Params& p, const RecT& R, const Gauss1D& g, float a, float gP, float B[],
                             const float4* __restrict__ qin = nullptr) {
     const int N = NI > 0 ? NI : p.n_intervals;
     PairOut o;
@@ -246,7 +287,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
     const float escale = g.Sig * 1.25331413731550025f;             // d tau_ij / d w-hat per erf difference
     const float tscale = g.what * escale;
     const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
-    Sample c, n;
+    Sample<typename BoundAdj<RecT>::Query> c, n;
     float4 qa = make_float4(0.0f, 0.0f, 0.0f, 0.0f), qb = qa;
     if (SAVED) {
         qa = qin[0];
@@ -317,9 +358,7 @@ MB_HD PairOut pair_backward(const Params& p, const Recon& R, const Gauss1D& g, f
             }
         }
         // sample j is final: through its bound query to y_j and the moments
-        float gy = 0.0f;
-        query_adjoint(p, R, c.q, c.gtau, &gy, B);
-        c.gt = fmaf(gy, 2.0f * c.dg * R.inv_s, c.gt);
+        c.gt = fmaf(sample_query_adjoint(p, R, c.q, c.gtau, B), c.dg, c.gt);
         if (!c.clamped) {
             o.g_mu += c.gt;
             o.g_Sig = fmaf(c.gt, p.kappa * p.x_nodes[j], o.g_Sig);

@@ -146,8 +146,19 @@ MB_HD float trig_node_weight(const TrigRecon& T, float target, float a, float ta
     return isfinite(e.lam) ? e.lam : 0.0f;
 }
 
-// tau at warped depth gq in [0, 1] (angle psi = A gq).
-MB_HD float trig_optical_depth(const Params& p, const TrigRecon& T, float gq) {
+// A solved trigonometric bound query, kept for the adjoint.
+struct TrigQueryRec {
+    float psi;      // psi_w = A clamp(gq, 0, 1)
+    int j;          // band of Theta(psi_w) above the cut, 0..4 (left side when j <= 2)
+    int ns;         // nodes solved (0..2), nearest to z_w first
+    float x[2];     // their angles
+    bool inside;    // gq in (0, 1): psi_w moves with the warped depth
+};
+
+// tau at warped depth gq in [0, 1] (angle psi = A gq).  REC keeps the nodes.
+template <bool REC>
+MB_HD float trig_bound_query(const Params& p, const TrigRecon& T, float gq, TrigQueryRec* rec) {
+    if (REC) { rec->psi = 0.0f; rec->j = 0; rec->ns = 0; rec->x[0] = 0.0f; rec->x[1] = 0.0f; rec->inside = false; }
     if (T.m0 <= 0.0f) return 0.0f;
     const float psi_w = p.trig_A * fminf(fmaxf(gq, 0.0f), 1.0f);
     const TrigEval w = trig_eval(T, psi_w);
@@ -158,6 +169,7 @@ MB_HD float trig_optical_depth(const Params& p, const TrigRecon& T, float gq) {
     float acc = 0.0f;
     const bool left = j <= 2;
     const int ns = left ? j : 4 - j;
+    if (REC) { rec->psi = psi_w; rec->j = j; rec->ns = ns; rec->inside = gq > 0.0f && gq < 1.0f; }
     // nodes nearest to z_w first: each bounds the next one's bracket
     float edge = psi_w, th_edge = w.th;
 #pragma unroll 1
@@ -174,6 +186,10 @@ MB_HD float trig_optical_depth(const Params& p, const TrigRecon& T, float gq) {
             edge = node;
             th_edge = target;
         }
+        if (REC) {   // static indices keep the record in registers
+            if (k == 1) rec->x[0] = node;
+            else rec->x[1] = node;
+        }
     }
     const float w0 = w.lam;
     float L = left ? acc : 1.0f - w0 - acc;
@@ -181,50 +197,61 @@ MB_HD float trig_optical_depth(const Params& p, const TrigRecon& T, float gq) {
     return T.m0 * fmaf(p.beta, w0, L);
 }
 
-// Per-pixel reconstruction: normalise and bias the moments towards those of
-// the uniform distribution on the angles [0, A] (FP64), Levinson-Durbin for
-// the Verblunsky coefficients (the bias is raised x4 per attempt, as for the
-// power moments, while the Toeplitz matrix is not positive definite), then
-// Theta at the cut (FP32, the same evaluation the queries use).
-MB_HD void reconstruct_trig(const Params& p, const float I[NMOM], TrigRecon& T) {
-    typedef MB_RECON_T real;
-    T.m0 = I[0];
-    T.th_lo = 0.0f;
-    if (!(I[0] >= p.m_min) || !isfinite(I[0])) {
-        T.m0 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { T.ar[k] = 0.0f; T.ai[k] = 0.0f; T.rho2[k] = 1.0f; }
-        return;
-    }
+MB_HD float trig_optical_depth(const Params& p, const TrigRecon& T, float gq) {
+    return trig_bound_query<false>(p, T, gq, nullptr);
+}
+
+// Levinson-Durbin recursion of one attempt, with the states the adjoint
+// re-traces: the monic Szego polynomials Phi_k (coefficients P[k][0..k]),
+// their norms E_k, the numerators n_k = <1, z Phi_k> and g_k = n_k / E_k =
+// conj(alpha_k).
+template <typename real>
+struct LevTrace {
+    real cr[5], ci[5];          // biased normalised moments c_0..c_4
+    real Pr[4][5], Pi[4][5];    // Phi_k, k = 0..3
+    real E[5];                  // E_0..E_4
+    real nr[4], ni[4];          // n_k
+    real gr[4], gi[4];          // g_k = conj(alpha_k)
+};
+
+// Normalise and bias the moments, c_k = (1 - alpha) m_k / m0 + alpha c*_k,
+// and run Levinson-Durbin for the Verblunsky coefficients; the bias is raised
+// x4 per attempt (to at most 0.5) while some |alpha_k| reaches 1 (Toeplitz
+// matrix not positive definite).  Returns the bias used; tr (if given) holds
+// the final attempt.
+template <typename real>
+MB_HD real trig_verblunsky(const Params& p, const float I[NMOM], real vr[4], real vi[4], LevTrace<real>* tr) {
     const real inv0 = real(1) / (real)I[0];
     real alpha = (real)p.bias_alpha;
-    real vr[4] = {0, 0, 0, 0}, vi[4] = {0, 0, 0, 0};
+    LevTrace<real> t;
 #pragma unroll 1
     for (int attempt = 0; attempt < 8; ++attempt) {
-        real cr[5], ci[5];
-        cr[0] = 1;
-        ci[0] = 0;
+        t.cr[0] = 1;
+        t.ci[0] = 0;
 #pragma unroll
         for (int k = 1; k <= 4; ++k) {
-            cr[k] = (real(1) - alpha) * (real)I[2 * k - 1] * inv0 + alpha * (real)p.cstar_re[k - 1];
-            ci[k] = (real(1) - alpha) * (real)I[2 * k] * inv0 + alpha * (real)p.cstar_im[k - 1];
+            t.cr[k] = (real(1) - alpha) * (real)I[2 * k - 1] * inv0 + alpha * (real)p.cstar_re[k - 1];
+            t.ci[k] = (real(1) - alpha) * (real)I[2 * k] * inv0 + alpha * (real)p.cstar_im[k - 1];
         }
-        // monic Phi_k coefficients P[0..k]
         real Pr[5] = {1, 0, 0, 0, 0}, Pi[5] = {0, 0, 0, 0, 0};
         real E = 1;
         bool ok = true;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int jj = 0; jj < 5; ++jj) { t.Pr[k][jj] = Pr[jj]; t.Pi[k][jj] = Pi[jj]; }
+            t.E[k] = E;
             // conj(alpha_k) = <1, z Phi_k> / E_k = sum_j P_j c_{j+1} / E_k
             real nr = 0, ni = 0;
 #pragma unroll
             for (int jj = 0; jj <= 3; ++jj) {
                 if (jj <= k) {
-                    nr += Pr[jj] * cr[jj + 1] - Pi[jj] * ci[jj + 1];
-                    ni += Pr[jj] * ci[jj + 1] + Pi[jj] * cr[jj + 1];
+                    nr += Pr[jj] * t.cr[jj + 1] - Pi[jj] * t.ci[jj + 1];
+                    ni += Pr[jj] * t.ci[jj + 1] + Pi[jj] * t.cr[jj + 1];
                 }
             }
             const real gr = nr / E, gi = ni / E;     // conj(alpha_k)
+            t.nr[k] = nr; t.ni[k] = ni; t.gr[k] = gr; t.gi[k] = gi;
             // Phi_{k+1}[j] = Phi_k[j-1] - conj(alpha_k) conj(Phi_k[k-j])
             real Qr[5], Qi[5];
 #pragma unroll
@@ -247,9 +274,30 @@ MB_HD void reconstruct_trig(const Params& p, const float I[NMOM], TrigRecon& T) 
             if (!(r2 < real(1) - real(1e-9))) ok = false;
             E *= real(1) - r2;
         }
+        t.E[4] = E;
         if (ok || alpha >= real(0.5)) break;
         alpha = alpha * 4 < real(0.5) ? alpha * 4 : real(0.5);
     }
+    if (tr) *tr = t;
+    return alpha;
+}
+
+// Per-pixel reconstruction: normalise and bias the moments towards those of
+// the uniform distribution on the angles [0, A] and run Levinson-Durbin for
+// the Verblunsky coefficients (FP64, trig_verblunsky), then Theta at the cut
+// (FP32, the same evaluation the queries use).
+MB_HD void reconstruct_trig(const Params& p, const float I[NMOM], TrigRecon& T) {
+    typedef MB_RECON_T real;
+    T.m0 = I[0];
+    T.th_lo = 0.0f;
+    if (!(I[0] >= p.m_min) || !isfinite(I[0])) {
+        T.m0 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { T.ar[k] = 0.0f; T.ai[k] = 0.0f; T.rho2[k] = 1.0f; }
+        return;
+    }
+    real vr[4] = {0, 0, 0, 0}, vi[4] = {0, 0, 0, 0};
+    trig_verblunsky<real>(p, I, vr, vi, (LevTrace<real>*)nullptr);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         real r = sqrt(vr[k] * vr[k] + vi[k] * vi[k]);

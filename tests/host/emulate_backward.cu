@@ -3,14 +3,17 @@
 // host, the device functions the kernels run:
 //   forward: pair_quadrature;
 //   pass 1: pixel_adjoint, pair_backward, geometry_adjoint_compact,
-//           phi_monomials, finish_moment_adjoint;
-//   pass 2: moment_adjoint, geometry_adjoint_compact;
+//           phi_monomials, finish_moment_adjoint (trig_finish_adjoint);
+//   pass 2: moment_adjoint (trig_moment_adjoint), geometry_adjoint_compact;
 //   per record: expand_geometry, preprocess_bwd_one.
 // The per-record sums are plain host sums in place of the warp, shared-memory
 // and global reductions; binning, tiling and launches are left out.  With
 // argv[3] == "saved" the bound queries kept by the forward feed pass 1, else
 // pass 1 solves them again.  argv[4] (optional): N intervals (default 3; other
-// values run the runtime-N templates).
+// values run the runtime-N templates).  argv[5] (optional): moment basis (0
+// power, 1 trigonometric: trig_moments, reconstruct_trig, the trigonometric
+// pair_backward, trig_finish_adjoint and trig_moment_adjoint; queries are
+// always solved again).
 //
 // argv[1]: input file (as for emulate_forward, then float32 dL/drgb [h][w][3]
 // and dL/dP [h][w] of the region); argv[2]: output file (float32 gradients of
@@ -48,7 +51,7 @@ static void rd(FILE* f, T* x, size_t n) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 4 && argc != 5) return 2;
+    if (argc < 4 || argc > 6) return 2;
     const bool saved = strcmp(argv[3], "saved") == 0;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
@@ -74,7 +77,9 @@ int main(int argc, char** argv) {
     fclose(f);
     mb3dgs_config cfg;
     mb3dgs_config_default(&cfg);
-    if (argc == 5) cfg.n_intervals = atoi(argv[4]);
+    if (argc >= 5) cfg.n_intervals = atoi(argv[4]);
+    if (argc >= 6) cfg.basis = atoi(argv[5]);
+    const bool trig = cfg.basis == MB3DGS_BASIS_TRIG;
     Params p;
     make_params(&cfg, p);
     ViewTable vt;
@@ -105,17 +110,22 @@ int main(int argc, char** argv) {
         float acc[NMOM] = {0};
         for (int64_t i : mine) {
             const float* r = &rec[i * REC];
-            legendre_moments(p, pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], rl, r2), acc);
+            const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], rl, r2);
+            if (trig) trig_moments(p, g, acc);
+            else legendre_moments(p, g, acc);
         }
         Recon R;
-        reconstruct_pixel(p, acc, R);
+        TrigRecon TR;
+        if (trig) reconstruct_trig(p, acc, TR);
+        else reconstruct_pixel(p, acc, R);
         float S[3] = {0, 0, 0}, O = 0, Pen = 0;
         std::vector<float4> qs(mine.size() * nq);
         for (size_t k = 0; k < mine.size(); ++k) {
             const float* r = &rec[mine[k] * REC];
             const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], rl, r2);
-            const float Oi = p.n_intervals == 3 ? pair_quadrature<3, true>(p, R, g, &Pen, &qs[k * nq])
-                                                : pair_quadrature<0, true>(p, R, g, &Pen, &qs[k * nq]);
+            const float Oi = trig ? pair_quadrature<0, false, TrigRecon>(p, TR, g, &Pen)
+                             : p.n_intervals == 3 ? pair_quadrature<3, true>(p, R, g, &Pen, &qs[k * nq])
+                                                  : pair_quadrature<0, true>(p, R, g, &Pen, &qs[k * nq]);
             for (int c = 0; c < 3; ++c) S[c] += r[R_RGB + c] * Oi;
             O += Oi;
         }
@@ -130,7 +140,9 @@ int main(int argc, char** argv) {
             const Gauss1D g = pair_gaussian(r, dx, dy, rl, r2);
             const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
             PairOut po;
-            if (p.n_intervals == 3)
+            if (trig)
+                po = pair_backward<0, false, TrigRecon>(p, TR, g, a, pa.gP, B);
+            else if (p.n_intervals == 3)
                 po = saved ? pair_backward<3, true>(p, R, g, a, pa.gP, B, &qs[k * nq])
                            : pair_backward<3, false>(p, R, g, a, pa.gP, B);
             else
@@ -143,15 +155,20 @@ int main(int argc, char** argv) {
             for (int f2 = 0; f2 < NK_QUAD; ++f2) s_quad[mine[k] * NK_QUAD + f2] += c[f2];
         }
         float psi[NPOLY];
-        phi_monomials(R, B, psi);
-        finish_moment_adjoint(p, R, pa.gm0, psi);
+        if (trig) {
+            trig_finish_adjoint(p, acc, B, pa.gm0, psi);
+        } else {
+            phi_monomials(R, B, psi);
+            finish_moment_adjoint(p, R, pa.gm0, psi);
+        }
         // pass 2
         for (int64_t i : mine) {
             const float* r = &rec[i * REC];
             const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
             const Gauss1D g = pair_gaussian(r, dx, dy, rl, r2);
             float g_mu = 0.0f, g_Sig = 0.0f, g_what = 0.0f;
-            moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
+            if (trig) trig_moment_adjoint(p, g, psi, &g_mu, &g_Sig, &g_what);
+            else moment_adjoint(p, R, g, psi, &g_mu, &g_Sig, &g_what);
             float c[NK_MOM];
             for (int f2 = 0; f2 < NK_MOM; ++f2) c[f2] = 0.0f;
             geometry_adjoint_compact(r, dx, dy, rl, g, g_mu, g_Sig, g_what, c);

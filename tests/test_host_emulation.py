@@ -207,6 +207,35 @@ def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, 
     assert max(err.values()) <= 1e-3, (name, mode, err)
 
 
+@pytest.mark.parametrize("N", [3, 5])
+def test_host_emulated_trig_backward_matches_oracle_gradient(emulator_bwd, tmp_path, N):
+    """The trigonometric adjoint (Verblunsky-coefficient query adjoints,
+    reverse Levinson-Durbin, the reverse of Eq. 14) against the oracle's
+    autograd gradient through its trigonometric bounds."""
+    sc = scenes.tiny_scene(P=40, seed=9, deg=3, spread=0.5)
+    cam = scenes.look_at((0.1, 0.2, -2.0), width=48, height=40, fov_deg=55)
+    region = (0, 0, cam.width, cam.height)
+    rng = np.random.default_rng(1)
+    g_img = rng.normal(size=(cam.height, cam.width, 3))
+    gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
+    fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
+    _write_input(fin, sc, cam, region, extra=(g_img, gP_img))
+    subprocess.run([emulator_bwd, fin, fout, "recomputed", str(N), "1"], check=True, timeout=900)
+    d = np.fromfile(fout, np.float32).astype(np.float64)
+    shapes = [sc.means.shape, sc.scales.shape, sc.quats.shape, sc.weights.shape, sc.sh.shape]
+    got, o = {}, 0
+    for k, shp in zip(NAMES, shapes):
+        n = int(np.prod(shp))
+        got[k] = d[o:o + n]
+        o += n
+    ref = O.render_grad(sc, cam, oracle_config(n_intervals=N, basis="trig"), g_img, gP_img)
+    err = {k: float(np.linalg.norm(got[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
+    emax = {k: float(np.abs(got[k] - ref[k].reshape(-1)).max() / max(np.abs(ref[k]).max(), 1e-30)) for k in NAMES}
+    print("host-emulated trig backward N=%d rel-L2" % N, {k: "%.2e" % v for k, v in err.items()},
+          "max/max", {k: "%.2e" % v for k, v in emax.items()})
+    assert max(err.values()) <= 1e-3 and max(emax.values()) <= 1e-3, (N, err, emax)
+
+
 @pytest.fixture(scope="module")
 def emulator_fp32_preprocess(tmp_path_factory):
     nvcc = _nvcc()

@@ -1,6 +1,7 @@
 """The oracle's gradient (autograd through the FP64 oracle, roots
 differentiated implicitly) against central finite differences of the oracle
-loss, with the proxy rectangles held fixed."""
+loss, with the proxy rectangles held fixed: power moments (Eq. 10-12, N = 3)
+and trigonometric moments (Eq. 13-14, N = 5)."""
 import numpy as np
 import pytest
 import torch
@@ -19,13 +20,14 @@ def _perturbed(sc, name, idx, h):
     return s2
 
 
+@pytest.mark.parametrize("basis", ["power", "trig"])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_oracle_gradient_matches_central_differences(seed):
+def test_oracle_gradient_matches_central_differences(seed, basis):
     sc = scenes.tiny_scene(P=7, seed=30 + seed, spread=0.3, log_scale=(-1.7, 0.25), deg=1)
     sc = scenes.Scene(sc.means.astype(np.float64), sc.scales.astype(np.float64), sc.quats.astype(np.float64),
                       sc.weights.astype(np.float64), sc.sh.astype(np.float64), sc.sh_degree)
     cam = scenes.look_at((0.05, 0.1, -2.4), width=20, height=18, fov_deg=45)
-    cfg = O.OracleConfig(bg=(0.1, 0.2, 0.3))
+    cfg = O.OracleConfig(bg=(0.1, 0.2, 0.3), basis=basis, n_intervals=5 if basis == "trig" else 3)
     rng = np.random.default_rng(seed)
     g = rng.normal(size=(18, 20, 3))
     gP = rng.normal(size=(18, 20)) * 0.3
