@@ -378,17 +378,27 @@ def trig_canonical_representation(c, phi, n):
     z0 = torch.polar(torch.ones_like(phi), phi)
     v0 = z0[..., None] ** powers
     a = torch.linalg.solve(G, torch.conj(v0)[..., None])[..., 0]      # K(z, z0) = sum_j a_j z^j
-    comp = torch.zeros(a.shape[:-1] + (n, n), dtype=a.dtype)
-    comp[..., 1:, :-1] = torch.eye(n - 1, dtype=a.dtype)
-    comp[..., :, -1] = -a[..., :n] / a[..., n:n + 1]
-    r = torch.linalg.eigvals(comp)
-    for _ in range(3):                                                  # Newton polish in FP64
-        p = torch.zeros_like(r) + a[..., n:n + 1]
+
+    def horner(coef, r):
+        p = torch.zeros_like(r) + coef[..., n:n + 1]
         dp = torch.zeros_like(r)
         for k in range(n - 1, -1, -1):
             dp = dp * r + p
-            p = p * r + a[..., k:k + 1]
-        r = r - p / dp
+            p = p * r + coef[..., k:k + 1]
+        return p, dp
+
+    with torch.no_grad():
+        ad = a.detach()
+        comp = torch.zeros(ad.shape[:-1] + (n, n), dtype=ad.dtype)
+        comp[..., 1:, :-1] = torch.eye(n - 1, dtype=ad.dtype)
+        comp[..., :, -1] = -ad[..., :n] / ad[..., n:n + 1]
+        r0 = torch.linalg.eigvals(comp)
+        for _ in range(3):                                              # Newton polish in FP64
+            p, dp = horner(ad, r0)
+            r0 = r0 - p / dp
+    # one Newton step with a live graph: exact implicit derivative of the roots
+    p, dp = horner(a, r0)
+    r = r0 - p / dp.detach()
     z = torch.cat([z0[..., None], r], -1)
     V = z[..., :, None] ** powers                                       # (..., n+1 nodes, n+1)
     sol = torch.linalg.solve(G[..., None, :, :], torch.conj(V)[..., None])[..., 0]

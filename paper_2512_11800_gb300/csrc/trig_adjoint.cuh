@@ -61,7 +61,10 @@ MB_HD void szego_trace(const TrigRecon& T, float psi, SzegoTrace& t) {
         const float iE = fdiv_(1.0f, E);
         t.pr[k + 1] = pr; t.pi[k + 1] = pi; t.sr[k + 1] = sr; t.si[k + 1] = si;
         t.iE[k + 1] = iE;
-        t.Q[k + 1] = fmaf(pr, pr, pi * pi) * iE;
+        // |Phi_k|^2 / E_k scaled before squaring: |Phi_k| can be ~1e-24 next to
+        // an atom of a concentrated measure, where its square underflows
+        const float rs = sqrtf(iE), qr = pr * rs, qi = pi * rs;
+        t.Q[k + 1] = fmaf(qr, qr, qi * qi);
         K += t.Q[k + 1];
         dK = fmaf(2.0f * fmaf(pr, dpr, pi * dpi), iE, dK);
     }
@@ -75,9 +78,16 @@ MB_HD void szego_trace(const TrigRecon& T, float psi, SzegoTrace& t) {
 // dL/dIm alpha_k to A[5 + k] (rho_k = 1 - |alpha_k|^2 included).  Complex
 // adjoints are carried as x-hat = dL/dRe x + i dL/dIm x.
 MB_HD void szego_adjoint(const TrigRecon& T, const SzegoTrace& t, float gK, float gTh, float A[NTRIG_ADJ]) {
-    // Theta = 5 psi - 2 arg Phi_4^*: S-hat_4 = -2 gTh i S_4 / |S_4|^2
-    const float is4 = fdiv_(1.0f, fmaf(t.sr[4], t.sr[4], t.si[4] * t.si[4]));
-    float Shr = 2.0f * gTh * t.si[4] * is4, Shi = -2.0f * gTh * t.sr[4] * is4;
+    // Theta = 5 psi - 2 arg Phi_4^*: S-hat_4 = -2 gTh i S_4 / |S_4|^2, formed
+    // from S_4 / max(|Re|, |Im|) (|S_4|^2 itself can underflow)
+    float Shr = 0.0f, Shi = 0.0f;
+    const float sm = fmaxf(fabsf(t.sr[4]), fabsf(t.si[4]));
+    if (gTh != 0.0f && sm > 0.0f) {
+        const float ism = 1.0f / sm, ur = t.sr[4] * ism, ui = t.si[4] * ism;
+        const float f = 2.0f * gTh * ism / fmaf(ur, ur, ui * ui);
+        Shr = f * ui;
+        Shi = -f * ur;
+    }
     float Phr = 0.0f, Phi = 0.0f;
     float qsum = 0.0f;   // sum_{m > k} |Phi_m|^2 / E_m
 #pragma unroll
@@ -108,9 +118,15 @@ MB_HD void szego_adjoint(const TrigRecon& T, const SzegoTrace& t, float gK, floa
 // Adjoint of one trigonometric bound query with dL/dtau = gq: adds to the
 // pixel's A (dL/dm0 at fixed alpha in A[0], the alpha adjoints after it) and
 // dL/d(warped depth) to *geta.
+// A query whose derivative is not finite in FP32 (z_w or a node on top of an
+// atom of a nearly discrete measure, where Theta' overflows) contributes
+// nothing.
 MB_HD void trig_query_adjoint(const Params& p, const TrigRecon& T, const TrigQueryRec& q, float gq, float* geta,
-                              float A[NTRIG_ADJ]) {
+                              float Apix[NTRIG_ADJ]) {
     if (T.m0 <= 0.0f || gq == 0.0f) return;
+    float A[NTRIG_ADJ];
+#pragma unroll
+    for (int k = 0; k < NTRIG_ADJ; ++k) A[k] = 0.0f;
     const bool left = q.j <= 2;
     const float s = left ? 1.0f : -1.0f;
     const float cw = left ? p.beta : p.beta - 1.0f;
@@ -125,7 +141,6 @@ MB_HD void trig_query_adjoint(const Params& p, const TrigRecon& T, const TrigQue
         const float lam = fdiv_(1.0f, t.K);
         const float dlam = -t.dK * lam * lam;
         const float rk = fdiv_(dlam, t.dth);
-        if (!isfinite(lam) || !isfinite(rk)) continue;
         F = fmaf(s, lam, F);
         ratio += rk;
         szego_adjoint(T, t, -gm * s * lam * lam, -gm * s * rk, A);
@@ -134,11 +149,20 @@ MB_HD void trig_query_adjoint(const Params& p, const TrigRecon& T, const TrigQue
     const float lw = fdiv_(1.0f, t.K);
     F = fmaf(cw, lw, F);
     szego_adjoint(T, t, -gm * cw * lw * lw, gm * s * ratio, A);
-    A[0] = fmaf(gq, F, A[0]);
+    A[0] = gq * F;
+    float ge = 0.0f;
     if (q.inside) {
         const float dlw = -t.dK * lw * lw;
-        *geta = fmaf(gm * p.trig_A, fmaf(cw, dlw, s * ratio * t.dth), *geta);
+        const float nodes = ratio != 0.0f ? s * ratio * t.dth : 0.0f;
+        ge = gm * p.trig_A * fmaf(cw, dlw, nodes);
     }
+    bool ok = isfinite(ge);
+#pragma unroll
+    for (int k = 0; k < NTRIG_ADJ; ++k) ok = ok && isfinite(A[k]);
+    if (!ok) return;
+#pragma unroll
+    for (int k = 0; k < NTRIG_ADJ; ++k) Apix[k] += A[k];
+    *geta += ge;
 }
 
 // Per-pixel moment adjoint: from the alpha adjoints (A) through reverse-mode

@@ -128,6 +128,8 @@ def _rel_errors(gg, ref):
     out = {}
     for k in NAMES:
         a, b = gg[k], ref[k].reshape(-1)
+        assert np.isfinite(b).all(), ("oracle gradient not finite", k)
+        assert np.isfinite(a).all(), ("GPU gradient not finite", k, int((~np.isfinite(a)).sum()))
         scale = max(float(np.abs(b).max()), 1e-30)
         out[k] = max(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)), float(np.abs(a - b).max()) / scale)
     return out
