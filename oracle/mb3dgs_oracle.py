@@ -345,7 +345,7 @@ def trig_gaussian_moments(mu, Sigma, w_hat, cfg: OracleConfig, erfc_fn=None):
     one_minus_erf = erfc_fn(re, im)
     mag = (w_hat * math.sqrt(math.pi / 2.0) * Sigma)[..., None] * torch.exp(-0.5 * (Sigma[..., None] * beta) ** 2)
     phase = alpha * a[..., None]
-    return torch.polar(mag, phase) * one_minus_erf
+    return torch.complex(mag * torch.cos(phase), mag * torch.sin(phase)) * one_minus_erf
 
 
 def trig_biased_moments(m, cfg: OracleConfig):
