@@ -337,8 +337,7 @@ def run_single(args, dist, rank, world, dev):
                                 tau_table=args.tau_table), device=dev)
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
-    # the tabulated transmittance is forward only
-    with_bwd = not args.forward_only and not args.tau_table
+    with_bwd = not args.forward_only
     fr = Frame(R, g, cam, target, save_queries=with_bwd)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -631,7 +630,7 @@ def main():
                     help="moment basis; trig (Eq. 13-14) reports no roofline (its node solve has no fixed op count)")
     ap.add_argument("--n-intervals", type=int, default=3)
     ap.add_argument("--tau-table", type=int, default=0,
-                    help="tabulated transmittance with this many knots a segment (forward only; 0: off)")
+                    help="tabulated transmittance with this many knots a segment (0: off)")
     ap.add_argument("--moment-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="storage of the per-pixel moments (accumulation is FP32 in every case)")
     args = ap.parse_args()

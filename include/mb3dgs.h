@@ -112,14 +112,15 @@ typedef struct mb3dgs_config {
                            Ignored with the TRIG basis. */
     int basis;          /* MB3DGS_BASIS_*; default POWER */
     float trig_theta;   /* TRIG: wrapping angle theta in (0, 2 pi) (reading); pi/2 */
-    int tau_table;      /* POWER, forward only: 0 (default) solves every bound query of the
-                           quadrature pass; M in [8, 128] has mb3dgs_reconstruct_transmittance
+    int tau_table;      /* POWER: 0 (default) solves every bound query of the quadrature
+                           pass; M in [8, 128] has mb3dgs_reconstruct_transmittance
                            tabulate tau(eta) and dtau/deta per pixel at M + 1 knots on each of
                            the (at most five) segments between the Gauss nodes in [0, 1],
                            and the quadrature pass interpolates them (cubic Hermite) instead
                            (40 (M + 1) bytes a pixel).  An approximation of Eq. 8: its error
                            against the solved bounds falls like M^-4.  The adjoint calls
-                           return MB3DGS_ERR_UNSUPPORTED while it is on. */
+                           differentiate the solved bounds that the table approximates
+                           (pass 1 solves its queries again; query_capacity is ignored). */
 } mb3dgs_config;
 
 /* Device pointers, caller-owned, layout as in the file comment. */

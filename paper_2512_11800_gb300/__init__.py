@@ -52,7 +52,8 @@ class RasterConfig:
     # moment basis: "power" (Eq. 10-12) or "trig" (Eq. 13-14)
     basis: str = "power"
     trig_theta: float = 0.5 * np.pi   # wrapping angle of the trigonometric moments
-    # tabulated transmittance (forward only): M knots a segment, 0 = solve every query
+    # tabulated transmittance: M knots a segment, 0 = solve every query (the backward
+    # differentiates the solved bounds the table approximates)
     tau_table: int = 0
 
     def to_c(self) -> B.Config:

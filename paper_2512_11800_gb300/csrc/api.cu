@@ -430,7 +430,6 @@ static int check_grads(const mb3dgs_gaussians* g, const mb3dgs_gaussian_grads* g
 int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                                int64_t pair_capacity, void* ws, size_t ws_bytes, const float* d_dL_drgb,
                                const float* d_dL_dpenalty, const float* d_dL_dT, mb3dgs_stream_t stream) {
-    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
@@ -442,7 +441,6 @@ int mb3dgs_backward_quadrature(const mb3dgs_config* cfg, const mb3dgs_camera* ca
 
 int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views, int64_t P,
                             int64_t pair_capacity, void* ws, size_t ws_bytes, mb3dgs_stream_t stream) {
-    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
@@ -453,7 +451,6 @@ int mb3dgs_backward_moments(const mb3dgs_config* cfg, const mb3dgs_camera* cams,
 int mb3dgs_backward_preprocess(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3dgs_camera* cams,
                                int n_views, void* ws, size_t ws_bytes, int64_t pair_capacity,
                                const mb3dgs_gaussian_grads* grads, mb3dgs_stream_t stream) {
-    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     int rc = check_grads(g, grads);
     if (rc) return rc;
     Ctx c;
@@ -468,7 +465,6 @@ int mb3dgs_backward(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const m
                     void* ws, size_t ws_bytes, int64_t pair_capacity, const float* d_dL_drgb,
                     const float* d_dL_dpenalty, const float* d_dL_dT, const mb3dgs_gaussian_grads* grads,
                     mb3dgs_stream_t stream) {
-    if (cfg && cfg->tau_table != 0) return MB3DGS_ERR_UNSUPPORTED;      // tabulated queries: forward only
     int rc = check_grads(g, grads);
     if (rc) return rc;
     if (!d_dL_drgb) return MB3DGS_ERR_INVALID_ARG;

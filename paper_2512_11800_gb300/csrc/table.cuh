@@ -11,8 +11,10 @@
 // segment.  The knots are Chebyshev-Lobatto spaced, u_i = (1 - cos(pi i / M))
 // / 2 of the segment: tau changes fastest next to the nodes (the atoms of a
 // concentrated measure sit there), where this spacing puts its knots (host
-// study: a few times smaller error than equal spacing at the same M).  The table replaces only the forward queries;
-// the adjoint needs the roots themselves and is not offered with a table.
+// study: a few times smaller error than equal spacing at the same M).  The
+// table replaces only the forward queries: the adjoint needs the roots
+// themselves, so with a table it solves them again and differentiates the
+// solved bounds that the table approximates.
 #pragma once
 #include "backward.cuh"
 
