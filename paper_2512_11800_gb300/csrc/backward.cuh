@@ -288,83 +288,112 @@ MB_HD PairOut pair_backward(const Params& p, const RecT& R, const Gauss1D& g, fl
     const float tscale = g.what * escale;
     const float dscale = g.what * g.Sig * 1.41421356237309505f;   // d tau_ij / d b = dscale e^{-b^2}
     Sample<typename BoundAdj<RecT>::Query> c, n;
-    float4 qa = make_float4(0.0f, 0.0f, 0.0f, 0.0f), qb = qa;
-    if (SAVED) {
-        qa = qin[0];
-        qb = qin[1];
-    }
-    load_sample<SAVED>(p, R, g, isq, 0, qa, c);
     // T_j = e^{-tau_j}, carried: T_{j+1} = T_j e^{-dtau_j} (e^{-dtau} = 1 - dtau ph)
-    float Tc = exp_(-c.tau), Tn = Tc;
-#pragma unroll 1
-    for (int j = 0; j <= N; ++j) {
-        if (j < N) {
-            load_sample<SAVED>(p, R, g, isq, j + 1, qb, n);
-            if (SAVED && j + 2 <= N) qb = qin[j + 2];
-            // interval j: term = T_j ph(dtau) sig_j Delta_j and the penalty v^2
-            const float Delta = n.t - c.t;
-            const float dtr = n.tau - c.tau;
-            const bool pos = dtr > 0.0f;
-            const float dtau = pos ? dtr : 0.0f;
-            const float Tj = Tc;
-            const float d0 = c.t - g.mu;
-            const float e0 = c.gau;
-            const float sig = g.what * e0;
-            // ph(x) = (1 - e^-x)/x and ph'(x) = (e^-x - ph(x))/x: Taylor series
-            // below x = 0.05 (truncation < 5e-10), where e^-x - ph cancels
-            float ph, dph;
-            if (dtau < 0.05f) {
-                ph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, 1.0f / 120.0f, -1.0f / 24.0f), 1.0f / 6.0f), -0.5f),
-                          1.0f);
-                dph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, -1.0f / 144.0f, 1.0f / 30.0f), -0.125f), 1.0f / 3.0f),
-                           -0.5f);
-            } else {
-                // dtau >= 0.05: 1 - e^-x keeps its digits with the fast exponential
-                const float em = exp_(-dtau);
-                const float idt = fdiv_(1.0f, dtau);
-                ph = (1.0f - em) * idt;
-                dph = (em - ph) * idt;
-            }
-            Tn = Tj * fmaf(-dtau, ph, 1.0f);
-            const float term = Tj * ph * sig * Delta;
-            o.O += term;
-            const float tij = tscale * (n.erf - c.erf);
-            const float v = fmaxf(tij - dtau, 0.0f);
-            c.gtau -= a * term;
-            const float gdt = a * Tj * dph * sig * Delta - 2.0f * gP * v;
-            if (pos) {
-                n.gtau += gdt;
-                c.gtau -= gdt;
-            }
-            const float gsig = a * Tj * ph * Delta;
-            const float gD = a * Tj * ph * sig;
-            n.gt += gD;
-            c.gt -= gD;
-            const float sd = gsig * sig * d0 * iSig2;
-            c.gt -= sd;
-            o.g_mu += sd;
-            o.g_Sig += sd * d0 * iSig;
-            o.g_what += gsig * e0;
-            const float gtij = 2.0f * gP * v;
-            if (gtij != 0.0f) {
-                o.g_what += gtij * escale * (n.erf - c.erf);
-                o.g_Sig += gtij * tij * iSig;
-                const float c1 = gtij * dscale * n.gau;
-                const float c0 = -gtij * dscale * c.gau;
-                n.gt += c1 * isq;
-                c.gt += c0 * isq;
-                o.g_mu -= (c1 + c0) * isq;
-                o.g_Sig -= (c1 * n.b + c0 * c.b) * iSig;
-            }
+    float Tc = 0.0f, Tn = 0.0f;
+    // interval j between samples c = j and n = j + 1: term = T_j ph(dtau)
+    // sig_j Delta_j and the penalty v^2
+    auto interval = [&]() {
+        const float Delta = n.t - c.t;
+        const float dtr = n.tau - c.tau;
+        const bool pos = dtr > 0.0f;
+        const float dtau = pos ? dtr : 0.0f;
+        const float Tj = Tc;
+        const float d0 = c.t - g.mu;
+        const float e0 = c.gau;
+        const float sig = g.what * e0;
+        // ph(x) = (1 - e^-x)/x and ph'(x) = (e^-x - ph(x))/x: Taylor series
+        // below x = 0.05 (truncation < 5e-10), where e^-x - ph cancels
+        float ph, dph;
+        if (dtau < 0.05f) {
+            ph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, 1.0f / 120.0f, -1.0f / 24.0f), 1.0f / 6.0f), -0.5f),
+                      1.0f);
+            dph = fmaf(dtau, fmaf(dtau, fmaf(dtau, fmaf(dtau, -1.0f / 144.0f, 1.0f / 30.0f), -0.125f), 1.0f / 3.0f),
+                       -0.5f);
+        } else {
+            // dtau >= 0.05: 1 - e^-x keeps its digits with the fast exponential
+            const float em = exp_(-dtau);
+            const float idt = fdiv_(1.0f, dtau);
+            ph = (1.0f - em) * idt;
+            dph = (em - ph) * idt;
         }
-        // sample j is final: through its bound query to y_j and the moments
+        Tn = Tj * fmaf(-dtau, ph, 1.0f);
+        const float term = Tj * ph * sig * Delta;
+        o.O += term;
+        const float tij = tscale * (n.erf - c.erf);
+        const float v = fmaxf(tij - dtau, 0.0f);
+        c.gtau -= a * term;
+        const float gdt = a * Tj * dph * sig * Delta - 2.0f * gP * v;
+        if (pos) {
+            n.gtau += gdt;
+            c.gtau -= gdt;
+        }
+        const float gsig = a * Tj * ph * Delta;
+        const float gD = a * Tj * ph * sig;
+        n.gt += gD;
+        c.gt -= gD;
+        const float sd = gsig * sig * d0 * iSig2;
+        c.gt -= sd;
+        o.g_mu += sd;
+        o.g_Sig += sd * d0 * iSig;
+        o.g_what += gsig * e0;
+        const float gtij = 2.0f * gP * v;
+        if (gtij != 0.0f) {
+            o.g_what += gtij * escale * (n.erf - c.erf);
+            o.g_Sig += gtij * tij * iSig;
+            const float c1 = gtij * dscale * n.gau;
+            const float c0 = -gtij * dscale * c.gau;
+            n.gt += c1 * isq;
+            c.gt += c0 * isq;
+            o.g_mu -= (c1 + c0) * isq;
+            o.g_Sig -= (c1 * n.b + c0 * c.b) * iSig;
+        }
+    };
+    // sample j (c) is final: through its bound query to y_j and the moments
+    auto sample_final = [&](int j) {
         c.gt = fmaf(sample_query_adjoint(p, R, c.q, c.gtau, B), c.dg, c.gt);
         if (!c.clamped) {
             o.g_mu += c.gt;
             o.g_Sig = fmaf(c.gt, p.kappa * p.x_nodes[j], o.g_Sig);
         }
-        c = n;
-        Tc = Tn;
+    };
+    if (SAVED) {
+        // kept queries: read one sample ahead of their use
+        float4 qa = qin[0], qb = qin[1];
+        load_sample<SAVED>(p, R, g, isq, 0, qa, c);
+        Tc = exp_(-c.tau);
+        Tn = Tc;
+#pragma unroll 1
+        for (int j = 0; j <= N; ++j) {
+            if (j < N) {
+                load_sample<SAVED>(p, R, g, isq, j + 1, qb, n);
+                if (j + 2 <= N) qb = qin[j + 2];
+                interval();
+            }
+            sample_final(j);
+            c = n;
+            Tc = Tn;
+        }
+    } else {
+        // queries solved here: iteration i loads sample i (i <= N), then
+        // handles interval i - 1 and sample i - 1 (i >= 1), so that the large
+        // solver code has one copy
+        const float4 none = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 1
+        for (int i = 0; i <= N + 1; ++i) {
+            if (i <= N) {
+                load_sample<SAVED>(p, R, g, isq, i, none, n);
+                if (i == 0) {
+                    Tc = exp_(-n.tau);
+                    Tn = Tc;
+                    c = n;
+                    continue;
+                }
+                interval();
+            }
+            sample_final(i - 1);
+            c = n;
+            Tc = Tn;
+        }
     }
     return o;
 }

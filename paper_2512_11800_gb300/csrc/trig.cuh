@@ -114,18 +114,21 @@ MB_HD TrigEval trig_eval(const TrigRecon& T, float psi) {
 // a staircase, where plain Newton can cycle).  It stops once the node is
 // within 2e-7 (relative) of the current point, and returns the Christoffel
 // weight evaluated there.
+// One evaluation site in the loop (the code is large: a single copy keeps
+// the adjoint kernel's hot loop in the instruction cache).
 MB_HD float trig_node_weight(const TrigRecon& T, float target, float a, float ta, float b, float tb, float* node) {
     float x = a + (b - a) * fminf(fmaxf(fdiv_(target - ta, tb - ta), 0.0f), 1.0f);
     float dx_old = b - a, dx = dx_old;
     const float h_floor = 5e-7f * (1.0f + fabsf(target));   // FP32 resolution of Theta
     TrigEval e;
     e.lam = 0.0f;
+    bool last = false;   // the step just taken was below the tolerance: this evaluation is the final one
 #pragma unroll 1
-    for (int it = 0; it < 32; ++it) {
+    for (int it = 0; it < 33; ++it) {
         e = trig_eval(T, x);
         const float h = e.th - target;
         const float tol = 2e-7f * (1.0f + fabsf(x));
-        if (fabsf(h) <= fmaxf(tol * e.dth, h_floor)) break;
+        if (last || it == 32 || fabsf(h) <= fmaxf(tol * e.dth, h_floor)) break;
         if (h > 0.0f) b = x;
         else a = x;
         const float xn = x - fdiv_(h, e.dth);
@@ -137,10 +140,7 @@ MB_HD float trig_node_weight(const TrigRecon& T, float target, float a, float ta
             dx = xn - x;
             x = xn;
         }
-        if (fabsf(dx) < tol) {
-            e = trig_eval(T, x);
-            break;
-        }
+        last = fabsf(dx) < tol;
     }
     *node = x;
     return isfinite(e.lam) ? e.lam : 0.0f;

@@ -133,29 +133,35 @@ MB_HD void trig_query_adjoint(const Params& p, const TrigRecon& T, const TrigQue
     const float gm = gq * T.m0;
     float F = left ? 0.0f : 1.0f;
     float ratio = 0.0f;   // sum_k lam'(psi_k) / Theta'(psi_k)
-    SzegoTrace t;
+    float ge = 0.0f;
+    // the solved nodes first (their seeds need only their own angle), z_w
+    // last (its Theta seed sums the nodes' ratios); one copy of the sweeps
 #pragma unroll 1
-    for (int r = 0; r < 2; ++r) {
-        if (r >= q.ns) break;
-        szego_trace(T, r == 0 ? q.x[0] : q.x[1], t);
+    for (int r = 0; r <= q.ns; ++r) {
+        const bool w = r == q.ns;
+        SzegoTrace t;
+        szego_trace(T, w ? q.psi : (r == 0 ? q.x[0] : q.x[1]), t);
         const float lam = fdiv_(1.0f, t.K);
         const float dlam = -t.dK * lam * lam;
-        const float rk = fdiv_(dlam, t.dth);
-        F = fmaf(s, lam, F);
-        ratio += rk;
-        szego_adjoint(T, t, -gm * s * lam * lam, -gm * s * rk, A);
+        float gK, gTh;
+        if (w) {
+            F = fmaf(cw, lam, F);
+            gK = -gm * cw * lam * lam;
+            gTh = gm * s * ratio;
+            if (q.inside) {
+                const float nodes = ratio != 0.0f ? s * ratio * t.dth : 0.0f;
+                ge = gm * p.trig_A * fmaf(cw, dlam, nodes);
+            }
+        } else {
+            const float rk = fdiv_(dlam, t.dth);
+            F = fmaf(s, lam, F);
+            ratio += rk;
+            gK = -gm * s * lam * lam;
+            gTh = -gm * s * rk;
+        }
+        szego_adjoint(T, t, gK, gTh, A);
     }
-    szego_trace(T, q.psi, t);
-    const float lw = fdiv_(1.0f, t.K);
-    F = fmaf(cw, lw, F);
-    szego_adjoint(T, t, -gm * cw * lw * lw, gm * s * ratio, A);
     A[0] = gq * F;
-    float ge = 0.0f;
-    if (q.inside) {
-        const float dlw = -t.dK * lw * lw;
-        const float nodes = ratio != 0.0f ? s * ratio * t.dth : 0.0f;
-        ge = gm * p.trig_A * fmaf(cw, dlw, nodes);
-    }
     bool ok = isfinite(ge);
 #pragma unroll
     for (int k = 0; k < NTRIG_ADJ; ++k) ok = ok && isfinite(A[k]);
