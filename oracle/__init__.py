@@ -7,3 +7,4 @@ shares no code with it; the only common module is the seeded input
 generator ``scenes``.
 """
 from .mb3dgs_oracle import *  # noqa: F401,F403
+from . import mb3dgs_adc as adc  # noqa: F401
