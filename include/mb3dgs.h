@@ -335,6 +335,85 @@ typedef struct mb3dgs_alu_peaks {
  * allocates no device memory. */
 int mb3dgs_probe_alu_peaks(mb3dgs_alu_peaks* out, mb3dgs_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Adaptive density control (Sec. 3.4 "Training and Densification"; App. D
+ * "Adaptive Density Control"): the per-Gaussian rules a training loop runs
+ * between optimiser steps.  All arrays are device, SoA as mb3dgs_gaussians
+ * (scales after exp, weights after softplus); all calls are asynchronous on
+ * the stream and allocate nothing.
+ * ------------------------------------------------------------------------- */
+typedef struct mb3dgs_adc_config {
+    float grad_threshold;   /* densify when |sum_t |dL/dmean|| / n_visible >= this; 1e-4 (App. D) */
+    float prune_opacity;    /* prune a resulting particle whose view-independent opacity is below
+                               this; 0.005 (the 3DGS rule the paper keeps) */
+    float percent_dense;    /* clone when max(s) <= percent_dense x scene_extent, else split; 0.01 */
+    float scene_extent;     /* caller's scene scale (3DGS: camera extent); 1 */
+    float big_world;        /* also prune when max(s) > big_world x scene_extent; 0.1; 0 = off */
+    float split_gamma;      /* split: the largest scale times gamma; 0.6385502815 (App. D) */
+    float split_delta;      /* split: children at mean -/+ delta s_max v; 0.6128153091 (App. D) */
+} mb3dgs_adc_config;
+
+/* Mutable Gaussian arrays (outputs of mb3dgs_densify), capacity entries each. */
+typedef struct mb3dgs_gaussians_out {
+    float* means;
+    float* scales;
+    float* quats;
+    float* weights;
+    float* sh;
+    int64_t capacity;
+} mb3dgs_gaussians_out;
+
+int mb3dgs_adc_config_default(mb3dgs_adc_config* cfg);
+
+/* View-independent opacity (App. D): the opacity of a particle seen along its
+ * shortest axis through its centre, o = 1 - exp(-sqrt(2 pi) w min(s)).
+ * weights [P], scales [P,3] in; opacity [P] out. */
+int mb3dgs_view_independent_opacity(const float* d_weights, const float* d_scales, int64_t P, float* d_opacity,
+                                    mb3dgs_stream_t stream);
+
+/* Peak densities from opacities (App. D, with the average scale):
+ * w = -log(1 - o) / (sqrt(2 pi) avg(s)).  opacity [P] in [0, 1), scales [P,3]
+ * in; weights [P] out.  o >= 1 gives +inf. */
+int mb3dgs_init_weights(const float* d_opacity, const float* d_scales, int64_t P, float* d_weights,
+                        mb3dgs_stream_t stream);
+
+/* One step of the densification statistics (App. D, after AbsGS): for every
+ * visible particle abs_sum[i] += |dL/dmean_i| component-wise (float32) and
+ * count[i] += 1.  d_visible [P] (0/1 bytes) may be NULL: a particle is then
+ * visible when a component of its mean gradient is non-zero.  abs_sum [P,3]
+ * and count [P] are the caller's running buffers (zero them at the start). */
+int mb3dgs_accumulate_grad_stats(const float* d_dmeans, const uint8_t* d_visible, int64_t P, float* d_abs_sum,
+                                 int32_t* d_count, mb3dgs_stream_t stream);
+
+/* Device workspace bytes of mb3dgs_densify for P input particles. */
+int mb3dgs_densify_workspace_size(int64_t P, size_t* bytes);
+
+/* Clone / split / prune (App. D with the 3DGS rules):
+ *   grad_i = |abs_sum_i| / count_i (0 when count_i = 0);
+ *   grad_i >= grad_threshold and max(s_i) <= percent_dense x extent: clone,
+ *     the particle and its copy each with w_i / 2;
+ *   grad_i >= grad_threshold otherwise: split into two particles at
+ *     mean -/+ split_delta s_max v (v the axis of the largest scale s_max,
+ *     the first one on ties), that scale times split_gamma, the rest copied;
+ *   every resulting particle is kept unless its view-independent opacity is
+ *   below prune_opacity or max(s) > big_world x extent.
+ * Threshold tests run in float32 in a fixed operation order (no fused
+ * multiply-add), so that decisions are reproducible: the opacity test as
+ * sqrt(2 pi) w min(s) >= -log(1 - prune_opacity).
+ * Outputs keep the input order, each input's particles contiguous (clone:
+ * original then copy; split: minus then plus offset).  out->capacity must be
+ * at least 2 g->P; *d_P_out (device int64) receives the new count.
+ * d_action [P] (int8, may be NULL) receives 0 kept as is, 1 cloned, 2 split
+ * (before pruning); d_first [P] (int32, may be NULL) the index of input i's
+ * first output particle (its outputs are d_first[i] .. d_first[i+1] - 1, the
+ * last input's end being *d_P_out): the map for carrying per-particle
+ * optimiser state over.  P is limited to 2^30.  Errors:
+ * MB3DGS_ERR_INVALID_ARG for null arrays, capacity below 2P or a bad config;
+ * MB3DGS_ERR_WORKSPACE_TOO_SMALL. */
+int mb3dgs_densify(const mb3dgs_adc_config* cfg, const mb3dgs_gaussians* g, const float* d_abs_sum,
+                   const int32_t* d_count, void* ws, size_t ws_bytes, const mb3dgs_gaussians_out* out,
+                   int64_t* d_P_out, int8_t* d_action, int32_t* d_first, mb3dgs_stream_t stream);
+
 /* Number of tiles (cfg->tile_w x cfg->tile_h pixels) over all views (host only). */
 int64_t mb3dgs_num_tiles(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_views);
 

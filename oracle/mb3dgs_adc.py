@@ -19,8 +19,9 @@ step in numpy:
   steps the particle was visible, compared with 1e-4;
 * clone (small particles): the particle and its copy each carry w / 2;
 * split (large particles): two particles at mean +/- delta s_max v, v the
-  axis of the largest scale s_max, that scale multiplied by gamma, everything
-  else copied (gamma = 0.6385502815, delta = 0.6128153091, App. D);
+  axis of the largest scale s_max, that scale multiplied by gamma (in
+  float32, since the pruning test reads it), everything else copied
+  (gamma = 0.6385502815, delta = 0.6128153091, App. D);
 * pruning of every resulting particle whose view-independent opacity is
   below the threshold or whose largest scale exceeds big_world x extent
   (the 3DGS rules this ADC keeps).
@@ -131,7 +132,7 @@ def densify(cfg: ADCConfig, means, scales, quats, weights, sh, abs_sum, count):
             k = int(np.argmax(s))           # first index of the largest scale
             v = _rotmat(quats[i])[:, k]     # its axis (a column of R, Sigma = R S^2 R^T)
             s_new = s.copy()
-            s_new[k] = cfg.split_gamma * s[k]
+            s_new[k] = f(f(cfg.split_gamma) * f(s[k]))    # formed in float32: the pruning test reads it
             for sign in (-1.0, 1.0):
                 cands.append((np.asarray(means[i], np.float64) + sign * cfg.split_delta * s[k] * v, s_new, quats[i],
                               float(weights[i]), sh[i]))

@@ -16,7 +16,7 @@ import torch
 
 from . import _binding as B
 
-__all__ = ["RasterConfig", "GaussianTensors", "Rasterizer", "to_camera", "load_library", "render"]
+__all__ = ["RasterConfig", "GaussianTensors", "Rasterizer", "to_camera", "load_library", "render", "adc"]
 
 
 def load_library():
@@ -360,3 +360,6 @@ def render(rast: "Rasterizer", cams, means, scales, quats, weights, sh, sh_degre
     Backward runs the adjoint passes of mb3dgs_backward; it raises if the same
     Rasterizer rendered again in between (its workspace holds one forward)."""
     return _RenderFn.apply(rast, cams, sh_degree, means, scales, quats, weights, sh)
+
+
+from . import adc  # noqa: E402  (adaptive density control, Sec. 3.4 / App. D)

@@ -39,6 +39,17 @@ class GaussianGrads(C.Structure):
                 ("sh", C.c_void_p)]
 
 
+class AdcConfig(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("prune_opacity", C.c_float), ("percent_dense", C.c_float),
+                ("scene_extent", C.c_float), ("big_world", C.c_float), ("split_gamma", C.c_float),
+                ("split_delta", C.c_float)]
+
+
+class GaussiansOut(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("quats", C.c_void_p), ("weights", C.c_void_p),
+                ("sh", C.c_void_p), ("capacity", C.c_int64)]
+
+
 MOMENTS = {"f32": 0, "bf16": 1, "f16": 2}
 BASES = {"power": 0, "trig": 1}
 SCHEDULES = {"queue": 0, "grid": 1}
@@ -49,7 +60,8 @@ EXPORTS = ["mb3dgs_status_string", "mb3dgs_last_cuda_error", "mb3dgs_config_defa
            "mb3dgs_bin_tiles", "mb3dgs_accumulate_moments", "mb3dgs_reconstruct_transmittance", "mb3dgs_shade",
            "mb3dgs_render", "mb3dgs_render_noalloc", "mb3dgs_backward", "mb3dgs_backward_quadrature",
            "mb3dgs_backward_moments", "mb3dgs_backward_preprocess", "mb3dgs_get_status", "mb3dgs_get_pair_counts", "mb3dgs_autotune", "mb3dgs_debug_tile_lists", "mb3dgs_num_tiles", "mb3dgs_launch_count",
-           "mb3dgs_probe_alu_peaks"]
+           "mb3dgs_probe_alu_peaks", "mb3dgs_adc_config_default", "mb3dgs_view_independent_opacity",
+           "mb3dgs_init_weights", "mb3dgs_accumulate_grad_stats", "mb3dgs_densify_workspace_size", "mb3dgs_densify"]
 
 _lib = None
 
@@ -81,6 +93,12 @@ def _declare(lib):
         "mb3dgs_num_tiles": (i64, [cfg, cam, C.c_int]),
         "mb3dgs_launch_count": (i64, []),
         "mb3dgs_probe_alu_peaks": (C.c_int, [P(AluPeaks), vp]),
+        "mb3dgs_adc_config_default": (C.c_int, [P(AdcConfig)]),
+        "mb3dgs_view_independent_opacity": (C.c_int, [vp, vp, i64, vp, vp]),
+        "mb3dgs_init_weights": (C.c_int, [vp, vp, i64, vp, vp]),
+        "mb3dgs_accumulate_grad_stats": (C.c_int, [vp, vp, i64, vp, vp, vp]),
+        "mb3dgs_densify_workspace_size": (C.c_int, [i64, P(sz)]),
+        "mb3dgs_densify": (C.c_int, [P(AdcConfig), gs, vp, vp, vp, sz, P(GaussiansOut), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

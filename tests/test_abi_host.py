@@ -168,3 +168,37 @@ def test_workspace_size_is_monotone_in_pair_capacity(lib):
         mid = lo + (hi - lo + 1) // 2
         lo, hi = (mid, hi) if fits(mid) else (lo, mid - 1)
     assert fits(lo) and not fits(lo + 1)
+
+
+def test_adc_defaults_and_validation(lib):
+    """mb3dgs_adc_config_default holds the paper's printed density-control
+    constants (App. D) and the oracle's defaults; the calls validate their
+    arguments on the host (no device work)."""
+    import json
+    import oracle as O
+    from paper_2512_11800_gb300 import _binding as B
+    c = B.AdcConfig()
+    assert lib.mb3dgs_adc_config_default(C.byref(c)) == 0
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+    f32 = lambda x: float(C.c_float(x).value)
+    assert c.grad_threshold == f32(gold["adc_grad_threshold"]["value"])
+    assert c.split_gamma == f32(gold["split_gamma"]["value"]) and c.split_delta == f32(gold["split_delta"]["value"])
+    ref = O.adc.ADCConfig()
+    for k in ["prune_opacity", "percent_dense", "scene_extent", "big_world"]:
+        assert getattr(c, k) == f32(getattr(ref, k)), k
+    n = C.c_size_t(0)
+    assert lib.mb3dgs_densify_workspace_size(1000, C.byref(n)) == 0 and n.value >= 8000
+    assert lib.mb3dgs_densify_workspace_size(-1, C.byref(n)) == -1
+    g = B.Gaussians()
+    g.P = 10
+    out = B.GaussiansOut()
+    out.capacity = 19                                   # below 2P
+    assert lib.mb3dgs_densify(C.byref(c), C.byref(g), None, None, None, 0, C.byref(out), None, None, None,
+                              None) == -1
+    bad = B.AdcConfig()
+    lib.mb3dgs_adc_config_default(C.byref(bad))
+    bad.split_gamma = 1.5
+    out.capacity = 20
+    assert lib.mb3dgs_densify(C.byref(bad), C.byref(g), None, None, None, 0, C.byref(out), None, None, None,
+                              None) == -1
+    assert lib.mb3dgs_view_independent_opacity(None, None, 5, None, None) == -1

@@ -131,7 +131,7 @@ def test_split_moves_along_the_principal_axis():
             Rc = O.quat_to_rotmat(torch.as_tensor(out["quats"][j])).numpy()
             evc = np.linalg.eigvalsh(Rc @ np.diag(out["scales"][j] ** 2) @ Rc.T)
             expect = np.sort(np.concatenate([ev[:2], [ev[-1] * A.SPLIT_GAMMA ** 2]]))
-            assert np.allclose(evc, expect, rtol=1e-9)
+            assert np.allclose(evc, expect, rtol=1e-6, atol=0.0)   # gamma s_max is formed in float32
         assert np.allclose(out["means"][2 * i] + out["means"][2 * i + 1], 2 * m[i], atol=1e-12)
 
 
