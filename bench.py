@@ -8,12 +8,14 @@ target -> backward (quadrature/bound adjoint, moment adjoint, preprocessing
 adjoint).  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--forward-only] [--workload shells1M_1080p|batch16]
+                  [--forward-only] [--workload shells1M_1080p|batch16|adc]
 
 --workload batch16: the same scene seen by 16 views of uneven resolution
 (640x360 / 1280x720 / 1920x1080), the whole fwd+bwd step captured in one
 CUDA graph and replayed, next to 16 sequential single-view render+backward
-calls.
+calls.  --workload adc: one adaptive-density-control step on the scene's 1M
+Gaussians (gradient statistics, then clone / split / prune).  The default
+line carries short records of both.
 
 With N > 1 (launched by torchrun) every rank renders its own replica of the
 workload (the path has no data exchange); rank 0 prints the aggregate.
@@ -445,6 +447,7 @@ def run_single(args, dist, rank, world, dev):
         R._ws = None
         torch.cuda.empty_cache()
         line["batch16"] = run_batch16(args, None, rank, world, dev, summary=True)
+        line["adc"] = run_adc(args, None, rank, world, dev, summary=True)
     return line
 
 
@@ -614,13 +617,96 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
     )
 
 
+def run_adc(args, dist, rank, world, dev, summary=False):
+    """One step of the adaptive density control (Sec. 3.4, App. D) on the 1M
+    scene: accumulate one step of |dL/dmean| statistics, then clone / split /
+    prune into a preallocated set (C ABI, no host synchronisation inside the
+    timed steps).  HBM-bound: algorithmic bytes = P (44 statistics + 252 read)
+    + P_out 236 written per step.  summary=True: the short form nested in the
+    default line."""
+    from paper_2512_11800_gb300 import GaussianTensors
+    from paper_2512_11800_gb300 import _binding as B
+    lib = B.load()
+    sc, _ = scenes.workload(WORKLOAD)
+    g = GaussianTensors.from_scene(sc, dev)
+    P = g.P
+    rng = np.random.default_rng(13)
+    dmeans = torch.as_tensor((rng.normal(size=(P, 3)) * 6e-5).astype(np.float32), device=dev)
+    abs_sum = torch.zeros(P, 3, device=dev)
+    count = torch.zeros(P, dtype=torch.int32, device=dev)
+    K3 = 3 * (sc.sh_degree + 1) ** 2
+    cap = 2 * P
+    outs = [torch.empty(cap, 3, device=dev), torch.empty(cap, 3, device=dev), torch.empty(cap, 4, device=dev),
+            torch.empty(cap, device=dev), torch.empty(cap, K3, device=dev)]
+    o = B.GaussiansOut()
+    o.means, o.scales, o.quats, o.weights, o.sh = (t.data_ptr() for t in outs)
+    o.capacity = cap
+    nb = C.c_size_t(0)
+    B.check(lib.mb3dgs_densify_workspace_size(P, C.byref(nb)), "densify_workspace_size")
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device=dev)
+    p_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    action = torch.empty(P, dtype=torch.int8, device=dev)
+    cfg = B.AdcConfig()
+    lib.mb3dgs_adc_config_default(C.byref(cfg))
+    cfg.scene_extent = 3.0          # camera distance of the scene
+    gc = g.to_c()
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    vp = lambda t: C.c_void_p(t.data_ptr())
+
+    def step():
+        B.check(lib.mb3dgs_accumulate_grad_stats(vp(dmeans), None, P, vp(abs_sum), vp(count), sp), "grad_stats")
+        B.check(lib.mb3dgs_densify(C.byref(cfg), C.byref(gc), vp(abs_sum), vp(count), vp(ws), ws.numel(),
+                                   C.byref(o), vp(p_out), vp(action), None, sp), "densify")
+
+    for _ in range(args.warmup):
+        abs_sum.zero_()
+        count.zero_()
+        step()
+    torch.cuda.synchronize()
+    steps = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    l0 = lib.mb3dgs_launch_count()
+    for k in range(steps):
+        abs_sum.zero_()          # one statistics step before each densification (outside the events)
+        count.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lib.mb3dgs_launch_count() - l0
+    ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+    n_out = int(p_out.item())
+    acts = np.bincount(action.cpu().numpy().astype(np.int64), minlength=3)
+    bytes_step = P * (44 + 252) + n_out * 236
+    peak = measured_peaks().get("hbm_gbs")
+    achieved = bytes_step / (ms * 1e-3) / 1e9
+    roof = dict(kernel="statistics + densify (count, scan, write)", bound="hbm", achieved=achieved, peak=peak,
+                unit="GB/s", frac=achieved / peak if peak else None, traffic=None,
+                peak_note="peak = MEASURED_PEAKS.json hbm_gbs (copy); achieved = algorithmic bytes "
+                          "P (44 + 252) + P_out 236 per step / median step time")
+    res = dict(workload="adc_shells1M: %d Gaussians (SH 3), statistics + clone/split/prune" % P,
+               value=P / (ms * 1e-3) / 1e6, unit="Mgaussian/s", ms_per_step=ms, steps=steps,
+               P_out=n_out, actions=dict(kept=int(acts[0]), cloned=int(acts[1]), split=int(acts[2])),
+               gpu_launches=int(launches), roofline=roof)
+    if summary:
+        return res
+    line = dict(metric="Mgaussian/s of one adaptive density control step, 1M Gaussians", value=res["value"],
+                unit="Mgaussian/s", n_gpus=world, steps=steps, warmup=args.warmup, ms_per_step=ms,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config={"workload": "adc_shells1M", "gaussians": P, "sh_degree": sc.sh_degree,
+                        "l2": "inputs larger than L2 (236 MB parameters)"},
+                P_out=n_out, actions=res["actions"], roofline=roof, gpu_launches=int(launches))
+    return line if rank == 0 else None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.WORKLOADS) + ["batch16"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.WORKLOADS) + ["batch16", "adc"],
                     help="the default is the headline workload; the others are for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch16", action="store_true",
@@ -640,7 +726,7 @@ def main():
         return
     dist, rank, world = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
-    run = run_batch16 if args.workload == "batch16" else run_single
+    run = {"batch16": run_batch16, "adc": run_adc}.get(args.workload, run_single)
     line = run(args, dist, rank, world, dev)
     if line is not None:
         print(json.dumps(line))
