@@ -125,39 +125,61 @@ __global__ void k_densify_total(const int* __restrict__ n_out, const int* __rest
     *total = P > 0 ? (int64_t)off[P - 1] + n_out[P - 1] : 0;
 }
 
+// The small fields of a result are written by its input's thread; the SH
+// coefficients (192 bytes a particle at degree 3), copied once per result,
+// by the whole warp for one input at a time, so that loads and stores are
+// coalesced.
 __global__ void k_densify_write(AdcParams a, mb3dgs_gaussians g, const float* __restrict__ abs_sum,
                                 const int32_t* __restrict__ count, const int* __restrict__ off,
                                 mb3dgs_gaussians_out out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.P) return;
-    const AdcDecision d = adc_decide(a, g.scales, g.weights, abs_sum, count, i);
-    if (!d.keep[0]) return;
-    const int K3 = 3 * (g.sh_degree + 1) * (g.sh_degree + 1);
-    float m[3] = {g.means[3 * i], g.means[3 * i + 1], g.means[3 * i + 2]};
-    const float q[4] = {g.quats[4 * i], g.quats[4 * i + 1], g.quats[4 * i + 2], g.quats[4 * i + 3]};
-    float v[3] = {0.0f, 0.0f, 0.0f};
-    if (d.action == 2) {
-        // column k of R(q) (Sigma = R S^2 R^T): the axis of the largest scale
-        const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-        const float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
-        if (d.k == 0) { v[0] = 1.0f - 2.0f * (y * y + z * z); v[1] = 2.0f * (x * y + w * z); v[2] = 2.0f * (x * z - w * y); }
-        else if (d.k == 1) { v[0] = 2.0f * (x * y - w * z); v[1] = 1.0f - 2.0f * (x * x + z * z); v[2] = 2.0f * (y * z + w * x); }
-        else { v[0] = 2.0f * (x * z + w * y); v[1] = 2.0f * (y * z - w * x); v[2] = 1.0f - 2.0f * (x * x + y * y); }
-        const float step = a.delta * g.scales[3 * i + d.k];   // delta times the unsplit s_max
-        for (int c = 0; c < 3; ++c) v[c] *= step;
-    }
-    const int nres = d.action == 0 ? 1 : 2;
-    int64_t o = off[i];
-    for (int r = 0; r < nres; ++r) {
-        const float sign = r == 0 ? -1.0f : 1.0f;   // split: minus offset first
-        for (int c = 0; c < 3; ++c) {
-            out.means[3 * o + c] = d.action == 2 ? fmaf(sign, v[c], m[c]) : m[c];
-            out.scales[3 * o + c] = d.s[c];
+    const int lane = threadIdx.x & 31;
+    const bool active = i < g.P;
+    int nres = 0;
+    int64_t o = 0;
+    if (active) {
+        const AdcDecision d = adc_decide(a, g.scales, g.weights, abs_sum, count, i);
+        if (d.keep[0]) {
+            nres = d.action == 0 ? 1 : 2;
+            o = off[i];
+            const float m[3] = {g.means[3 * i], g.means[3 * i + 1], g.means[3 * i + 2]};
+            const float q[4] = {g.quats[4 * i], g.quats[4 * i + 1], g.quats[4 * i + 2], g.quats[4 * i + 3]};
+            float v[3] = {0.0f, 0.0f, 0.0f};
+            if (d.action == 2) {
+                // column k of R(q) (Sigma = R S^2 R^T): the axis of the largest scale
+                const float inv = rsqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+                const float w = q[0] * inv, x = q[1] * inv, y = q[2] * inv, z = q[3] * inv;
+                if (d.k == 0) { v[0] = 1.0f - 2.0f * (y * y + z * z); v[1] = 2.0f * (x * y + w * z); v[2] = 2.0f * (x * z - w * y); }
+                else if (d.k == 1) { v[0] = 2.0f * (x * y - w * z); v[1] = 1.0f - 2.0f * (x * x + z * z); v[2] = 2.0f * (y * z + w * x); }
+                else { v[0] = 2.0f * (x * z + w * y); v[1] = 2.0f * (y * z - w * x); v[2] = 1.0f - 2.0f * (x * x + y * y); }
+                const float step = a.delta * g.scales[3 * i + d.k];   // delta times the unsplit s_max
+                for (int c = 0; c < 3; ++c) v[c] *= step;
+            }
+            for (int r = 0; r < nres; ++r) {
+                const int64_t t = o + r;
+                const float sign = r == 0 ? -1.0f : 1.0f;   // split: minus offset first
+                for (int c = 0; c < 3; ++c) {
+                    out.means[3 * t + c] = d.action == 2 ? fmaf(sign, v[c], m[c]) : m[c];
+                    out.scales[3 * t + c] = d.s[c];
+                }
+                for (int c = 0; c < 4; ++c) out.quats[4 * t + c] = q[c];
+                out.weights[t] = d.w;
+            }
         }
-        for (int c = 0; c < 4; ++c) out.quats[4 * o + c] = q[c];
-        out.weights[o] = d.w;
-        for (int c = 0; c < K3; ++c) out.sh[(size_t)o * K3 + c] = g.sh[(size_t)i * K3 + c];
-        ++o;
+    }
+    const int K3 = 3 * (g.sh_degree + 1) * (g.sh_degree + 1);
+    unsigned todo = __ballot_sync(0xffffffffu, nres > 0);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const long long si = __shfl_sync(0xffffffffu, (long long)i, src);
+        const long long so = __shfl_sync(0xffffffffu, (long long)o, src);
+        const int n = __shfl_sync(0xffffffffu, nres, src);
+        for (int c = lane; c < K3; c += 32) {
+            const float x = g.sh[(size_t)si * K3 + c];
+            out.sh[(size_t)so * K3 + c] = x;
+            if (n == 2) out.sh[(size_t)(so + 1) * K3 + c] = x;
+        }
     }
 }
 
