@@ -562,7 +562,7 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
                     value=world * tot / (ms * 1e-3) / 1e6, unit="Mpixel/s", ms_per_step=ms, steps=args.steps,
                     sequential_ms_per_step=seq_ms, sequential_mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
                     speedup_vs_sequential=seq_ms / ms, pixels=tot, pixel_pairs=pairs,
-                    kept_queries_frac=fbs[0].qcap / max(pp, 1), gpu_launches=int(launches), status=st, clocks=clk)
+                    query_bytes=8 if R.cfg_c.compact_queries else 16, kept_queries_frac=fbs[0].qcap / max(pp, 1), gpu_launches=int(launches), status=st, clocks=clk)
 
     # end to end: inputs from pinned host memory into the graph's input
     # buffers, replay, rgb back to host
@@ -599,7 +599,8 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
         config={"workload": "batch16_shells1M", "gaussians": g.P, "views": [[c.width, c.height] for c in cams],
                 "pixels": tot, "pass": "forward+backward" if with_bwd else "forward",
                 "query_slots": fbs[0].qcap, "pixel_pairs": pp,
-                "kept_queries": "%.0f %% of the pixel pairs (60 %% of free device memory)" % (100.0 * fbs[0].qcap / max(pp, 1)),
+                "kept_queries": "%.0f %% of the pixel pairs (60 %% of free device memory), %d B a query"
+                                % (100.0 * fbs[0].qcap / max(pp, 1), 8 if R.cfg_c.compact_queries else 16),
                 "groups": groups,
                 "tiling": dict(tile=list(tuned[:2]), batch=tuned[2], schedule=tuned[3], tuned_ms=tuned[4]),
                 "graph": "whole step in one CUDA graph (one set of persistent launches over all 16 views)",

@@ -101,7 +101,8 @@ typedef struct mb3dgs_config {
     int schedule;
     int64_t query_capacity; /* (pixel, Gaussian) pair slots in which mb3dgs_shade keeps
                            the N+1 bound queries of every pair (16 (N+1) bytes a
-                           pair: 64 at N = 3) for mb3dgs_backward, which then
+                           pair: 64 at N = 3; 8 (N+1) with compact_queries) for
+                           mb3dgs_backward, which then
                            reads them instead of solving them again.  Pixels
                            are served in pixel order while all of a pixel's
                            pairs fit; the backward solves the queries of the
@@ -121,6 +122,12 @@ typedef struct mb3dgs_config {
                            against the solved bounds falls like M^-4.  The adjoint calls
                            differentiate the solved bounds that the table approximates
                            (pass 1 solves its queries again; query_capacity is ignored). */
+    int compact_queries; /* 0 (default): a kept bound query takes 16 bytes {tau, x_0, x_1,
+                           j | nroot}.  1: 8 bytes {tau, the roots as 13-bit positions in
+                           their brackets, j, nroot}; the backward restores each root by
+                           two Laguerre steps from its position (the results agree with
+                           the 16-byte form to rounding), so twice as many pairs keep
+                           their queries in the same memory. */
 } mb3dgs_config;
 
 /* Device pointers, caller-owned, layout as in the file comment. */

@@ -16,7 +16,7 @@ class Config(C.Structure):
                 ("bg", c_float3), ("moment_dtype", C.c_int), ("strict", C.c_int),
                 ("tile_w", C.c_int), ("tile_h", C.c_int), ("batch", C.c_int), ("schedule", C.c_int),
                 ("query_capacity", C.c_int64), ("basis", C.c_int), ("trig_theta", C.c_float),
-                ("tau_table", C.c_int)]
+                ("tau_table", C.c_int), ("compact_queries", C.c_int)]
 
 
 class Gaussians(C.Structure):

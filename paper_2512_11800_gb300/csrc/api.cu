@@ -59,6 +59,7 @@ static int check_cfg(const mb3dgs_config* c) {
     if (c->basis == MB3DGS_BASIS_TRIG && !(c->trig_theta > 0.0f && c->trig_theta < (float)(2.0 * M_PI)))
         return MB3DGS_ERR_INVALID_ARG;
     if (c->tau_table != 0 && (c->tau_table < 8 || c->tau_table > 128)) return MB3DGS_ERR_INVALID_ARG;
+    if (c->compact_queries != 0 && c->compact_queries != 1) return MB3DGS_ERR_INVALID_ARG;
     if (c->tau_table != 0 && c->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;
     if (c->tile_w != 0 || c->tile_h != 0) {
         const int tw = c->tile_w, th = c->tile_h;
@@ -159,7 +160,8 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     if (L.qcap > 0) {
         L.npp = take(sizeof(int) * (size_t)npix);
         L.pq_off = take(sizeof(long long) * (size_t)npix);
-        L.pq = take(sizeof(float) * 4 * (size_t)(cfg->n_intervals + 1) * (size_t)L.qcap);   // one float4 a query
+        const size_t qb = cfg->compact_queries ? 8 : 16;   // bytes a query
+        L.pq = take(qb * (size_t)(cfg->n_intervals + 1) * (size_t)L.qcap);
     }
     L.total = o;
     return MB3DGS_OK;
@@ -227,6 +229,7 @@ static void make_params(const mb3dgs_config* c, Params& p) {
     p.moment_dtype = c->moment_dtype;
     p.basis = c->basis;
     p.tab_m = c->basis == MB3DGS_BASIS_POWER ? c->tau_table : 0;
+    p.qbytes = c->compact_queries ? 8 : 16;
     if (c->basis == MB3DGS_BASIS_TRIG) {
         const double A = 2.0 * M_PI - (double)c->trig_theta;
         p.trig_A = (float)A;

@@ -67,7 +67,7 @@ __device__ __forceinline__ void finish_pixel(const Params& p, const TrigRecon&, 
 // SAVED: only the pixels whose bound queries the quadrature pass kept
 // (pq_off + npp <= qcap), read instead of solved; otherwise the pixels that
 // kept none (all pixels when qcap == 0), whose queries are solved again.
-template <int NI, bool SAVED, class RecT>
+template <int NI, bool SAVED, class RecT, int QB = 16>
 __global__ void __launch_bounds__(TPB, 2)
     k_bwd_quadrature(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                      const int32_t* __restrict__ ids, const int2* __restrict__ ranges, int64_t P, int64_t npix,
@@ -75,13 +75,13 @@ __global__ void __launch_bounds__(TPB, 2)
                      const float* __restrict__ saved, const float* __restrict__ dL_drgb,
                      const float* __restrict__ dL_dP, const float* __restrict__ dL_dT, float* __restrict__ psi_out,
                      float* __restrict__ grec, const int* __restrict__ npp, const long long* __restrict__ pq_off,
-                     const float4* __restrict__ pq, int64_t qcap) {
+                     const char* __restrict__ pq, int64_t qcap) {
     extern __shared__ float4 s_raw[];
     float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_BWD_FLOATS;
     float* s_sum = s_buf + WARP_STAGE_FLOATS;          // [32][NK_QUAD] compact sums of the chunk
     const bool any = sw->n_valid != 0;
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
-    const float4* q_end = SAVED ? pq + (size_t)qcap * nq : nullptr;   // end of the saved queries
+    const char* q_end = SAVED ? pq + (size_t)qcap * nq * QB : nullptr;   // end of the saved queries
     const int ridx = rs_index<NK_QUAD>(threadIdx.x & 31);   // compact sum this lane reduces
     int fp, fx0, fy0;
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(TPB, 2)
             c.inside = (off + npp[c.pix] <= qcap) == SAVED;   // this launch's pixels
         }
         if (!any || !__any_sync(0xffffffffu, c.inside)) c.end = c.start;
-        const float4* qp = nullptr;
+        const char* qp = nullptr;
         RecT R;
         PixelAdj pa;
         constexpr int NACC = BoundAdj<RecT>::NACC;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(TPB, 2)
             const float m0 = load_m0(p, moments, c.pix);
             pa = pixel_adjoint(p, m0, S, O, g, dL_dP ? dL_dP[c.pix] : 0.0f);
             if (dL_dT) pa.gm0 -= expf(-m0) * dL_dT[c.pix];   // T_final = e^{-m0}
-            if (SAVED) qp = pq + (size_t)off * nq;
+            if (SAVED) qp = pq + (size_t)off * nq * QB;
         }
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         for (int pos = c.start; pos < c.end; pos += 32) {
@@ -125,13 +125,13 @@ __global__ void __launch_bounds__(TPB, 2)
                 if (active) {
                     // the pixel's saved queries are contiguous in pair order: start
                     // fetching the next pair's into L2 while this one is processed
-                    if (SAVED && qp + 2 * nq <= q_end)
-                        asm volatile("prefetch.global.L2 [%0];" ::"l"(qp + nq));
+                    if (SAVED && qp + 2 * nq * QB <= q_end)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(qp + nq * QB));
                     const float dx = fpx - r[R_AX], dy = fpy - r[R_AY];
                     const Gauss1D g = pair_gaussian(r, dx, dy, c.rlen, c.r2);
                     const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
-                    const PairOut po = pair_backward<NI, SAVED, RecT>(p, R, g, a, pa.gP, B, qp);
-                    if (SAVED) qp += nq;
+                    const PairOut po = pair_backward<NI, SAVED, RecT, QB>(p, R, g, a, pa.gP, B, qp);
+                    if (SAVED) qp += nq * QB;
                     geometry_adjoint_compact(r, dx, dy, c.rlen, g, po.g_mu, po.g_Sig, po.g_what, acc);
                     acc[K_RGB + 0] = pa.gS[0] * po.O;
                     acc[K_RGB + 1] = pa.gS[1] * po.O;
@@ -412,6 +412,8 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
                       ? (p.n_intervals == 3   ? k_bwd_quadrature<3, false, TrigRecon>
                          : p.n_intervals == 5 ? k_bwd_quadrature<5, false, TrigRecon>
                                               : k_bwd_quadrature<0, false, TrigRecon>)
+                  : saved_q && p.qbytes == 8
+                      ? (p.n_intervals == 3 ? k_bwd_quadrature<3, true, Recon, 8> : k_bwd_quadrature<0, true, Recon, 8>)
                   : p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true, Recon> : k_bwd_quadrature<3, false, Recon>)
                                        : (saved_q ? k_bwd_quadrature<0, true, Recon> : k_bwd_quadrature<0, false, Recon>);
         if (!allow_dynamic_smem((const void*)k1, smem)) return MB3DGS_ERR_CUDA;
@@ -425,7 +427,7 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
             dL_drgb, dL_dP, dL_dT, reinterpret_cast<float*>(ws + L.dm), grec,
             kept ? reinterpret_cast<const int*>(ws + L.npp) : nullptr,
             kept ? reinterpret_cast<const long long*>(ws + L.pq_off) : nullptr,
-            kept ? reinterpret_cast<const float4*>(ws + L.pq) : nullptr, L.qcap);
+            kept ? ws + L.pq : nullptr, L.qcap);
     }
     return MB3DGS_OK;
 }

@@ -219,15 +219,31 @@ struct Sample {
 };
 
 // Optical depth of a sample at warped depth gj with its query record: read
-// from the kept query (SAVED, power moments only) or solved again.
-template <bool SAVED>
+// from the kept query (SAVED, power moments only; QB = 8: the compact form,
+// its roots restored by two Laguerre steps) or solved again.
+template <bool SAVED, int QB>
 MB_HD float sample_query(const Params& p, const Recon& R, float gj, float4 qv, QueryRec& q) {
-    if (SAVED) return unpack_query(qv, (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s, q);
+    if (SAVED) {
+        const float y = (fmaf(2.0f, gj, -1.0f) - R.c) * R.inv_s;
+        if (QB == 8) return unpack_query_compact(R, make_float2(qv.x, qv.y), y, q);
+        return unpack_query(qv, y, q);
+    }
     return bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q);
 }
-template <bool SAVED>
+template <bool SAVED, int QB>
 MB_HD float sample_query(const Params& p, const TrigRecon& T, float gj, float4, TrigQueryRec& q) {
     return trig_bound_query<true>(p, T, gj, &q);
+}
+
+// Kept query j of a pair (QB bytes each) as a float4 ({tau, bits} in x, y
+// for the compact form).
+template <int QB>
+MB_HD float4 load_kept_query(const char* __restrict__ q, int j) {
+    if (QB == 8) {
+        const float2 v = reinterpret_cast<const float2*>(q)[j];
+        return make_float4(v.x, v.y, 0.0f, 0.0f);
+    }
+    return reinterpret_cast<const float4*>(q)[j];
 }
 
 // Adjoint of a sample's bound query for dL/dtau = gq: adds to the pixel's
@@ -244,14 +260,14 @@ MB_HD float sample_query_adjoint(const Params& p, const TrigRecon& T, const Trig
     return ge;
 }
 
-template <bool SAVED, class RecT, class QR>
+template <bool SAVED, int QB, class RecT, class QR>
 MB_HD void load_sample(const Params& p, const RecT& R, const Gauss1D& g, float isq, int j, float4 qv, Sample<QR>& s) {
     const float raw = fmaf(p.kappa * g.Sig, p.x_nodes[j], g.mu);
     s.t = fminf(fmaxf(raw, p.t_near), p.t_far);
     s.clamped = s.t != raw;
     float gj;
     warp_g(p, s.t, gj, s.dg);
-    s.tau = sample_query<SAVED>(p, R, gj, qv, s.q);
+    s.tau = sample_query<SAVED, QB>(p, R, gj, qv, s.q);
     s.b = (s.t - g.mu) * isq;
     s.erf = p.x_erf[j];
     s.gau = p.x_gau[j];
@@ -266,15 +282,15 @@ MB_HD void load_sample(const Params& p, const RecT& R, const Gauss1D& g, float i
 // Recomputes the pair's quadrature (Eq. 7, App. B, App. D) and back-propagates
 // L_i = a O_i + gP P_i: accumulates the bound derivative Phi of the pixel into
 // B and returns the direct derivatives with respect to (mu, Sigma, w-hat).
-// With SAVED the bound queries come from the quadrature pass (qin, N+1 float4)
-// instead of being solved again.  Streamed over the samples: interval j is
+// With SAVED the bound queries come from the quadrature pass (qin, N+1 of QB
+// bytes) instead of being solved again.  Streamed over the samples: interval j is
 // processed once samples j and j+1 are loaded, after which sample j's
 // adjoints are final and go through its bound query (one copy of the query
 // code, no per-sample arrays).  Saved queries are read one sample ahead of
 // their use, so each load overlaps a whole interval's arithmetic.
-template <int NI, bool SAVED = false, class RecT = Recon>
+template <int NI, bool SAVED = false, class RecT = Recon, int QB = 16>
 MB_HD PairOut pair_backward(const Params& p, const RecT& R, const Gauss1D& g, float a, float gP, float B[],
-                            const float4* __restrict__ qin = nullptr) {
+                            const char* __restrict__ qin = nullptr) {
     const int N = NI > 0 ? NI : p.n_intervals;
     PairOut o;
     o.O = 0.0f;
@@ -358,15 +374,15 @@ MB_HD PairOut pair_backward(const Params& p, const RecT& R, const Gauss1D& g, fl
     };
     if (SAVED) {
         // kept queries: read one sample ahead of their use
-        float4 qa = qin[0], qb = qin[1];
-        load_sample<SAVED>(p, R, g, isq, 0, qa, c);
+        float4 qa = load_kept_query<QB>(qin, 0), qb = load_kept_query<QB>(qin, 1);
+        load_sample<SAVED, QB>(p, R, g, isq, 0, qa, c);
         Tc = exp_(-c.tau);
         Tn = Tc;
 #pragma unroll 1
         for (int j = 0; j <= N; ++j) {
             if (j < N) {
-                load_sample<SAVED>(p, R, g, isq, j + 1, qb, n);
-                if (j + 2 <= N) qb = qin[j + 2];
+                load_sample<SAVED, QB>(p, R, g, isq, j + 1, qb, n);
+                if (j + 2 <= N) qb = load_kept_query<QB>(qin, j + 2);
                 interval();
             }
             sample_final(j);
@@ -381,7 +397,7 @@ MB_HD PairOut pair_backward(const Params& p, const RecT& R, const Gauss1D& g, fl
 #pragma unroll 1
         for (int i = 0; i <= N + 1; ++i) {
             if (i <= N) {
-                load_sample<SAVED>(p, R, g, isq, i, none, n);
+                load_sample<SAVED, QB>(p, R, g, isq, i, none, n);
                 if (i == 0) {
                     Tc = exp_(-n.tau);
                     Tn = Tc;

@@ -86,6 +86,7 @@ struct Params {
     float trig_lo;         // cut -theta/2 (middle of the wrapping zone)
     float cstar_re[4], cstar_im[4];   // moments of the uniform distribution on [0, A] (bias target)
     int tab_m;             // knots per segment of the tabulated transmittance (0: off)
+    int qbytes;            // bytes of a kept bound query: 16, or 8 with compact queries
 };
 
 // Workspace layout (byte offsets), computed on the host.
@@ -119,7 +120,7 @@ struct Layout {
     size_t sched;       // SCHED_BYTES: per-launch tile queues, bucket counts and cursors
     size_t npp;         // int32 [NPIX] (pixel, Gaussian) pairs per pixel
     size_t pq_off;      // int64 [NPIX] exclusive scan of npp
-    size_t pq;          // float4 [qcap][N+1] saved bound queries {tau, x0, x1, j | nroot << 4}
+    size_t pq;          // [qcap][N+1] saved bound queries: float4 {tau, x0, x1, j | nroot << 4}, or 8-byte compact
     size_t tab_e;       // float [4][NPIX] segment edges of the tabulated transmittance
     size_t tab;         // float2 [5 (M+1)][NPIX] tabulated (tau, dtau/deta)
     int tab_m;          // knots per segment M (0: no table)
@@ -341,6 +342,29 @@ MB_HD float laguerre_step(float x, float f, float fp, float fpp, float lo, float
     return fminf(fmaxf(xn, lo), hi);
 }
 
+// K(x) = sum_k e_k pi_k(x) and its first two derivatives through the
+// three-term recurrence (the accurate form near a root).
+MB_HD void kernel_poly_d2(const Recon& R, const float e[5], float x, float& f, float& fp, float& fpp) {
+    float p0 = 1.0f, p1 = x - R.al[0];
+    float d0 = 0.0f, d1 = 1.0f;
+    float s0 = 0.0f, s1 = 0.0f;
+    f = e[0] + e[1] * p1;
+    fp = e[1];
+    fpp = 0.0f;
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+        const float xa = x - R.al[k];
+        const float b = R.be[k - 1];
+        float p2 = fmaf(xa, p1, -b * p0);
+        float d2 = fmaf(xa, d1, fmaf(-b, d0, p1));
+        float s2 = fmaf(xa, s1, fmaf(-b, s0, 2.0f * d1));
+        f = fmaf(e[k + 1], p2, f);
+        fp = fmaf(e[k + 1], d2, fp);
+        fpp = fmaf(e[k + 1], s2, fpp);
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2; s0 = s1; s1 = s2;
+    }
+}
+
 // Laguerre iteration towards the neighbouring root on one side.  For a
 // real-rooted polynomial the iterates move monotonically to the adjacent root
 // in the chosen direction, cubically near it.  All but the last step evaluate
@@ -360,22 +384,8 @@ MB_HD float laguerre(const Recon& R, const float e[5], const float c[5], float x
         }
         x = laguerre_step(x, f, d1, 2.0f * d2, lo, hi, right);
     }
-    float p0 = 1.0f, p1 = x - R.al[0];
-    float d0 = 0.0f, d1 = 1.0f;
-    float s0 = 0.0f, s1 = 0.0f;
-    float f = e[0] + e[1] * p1, fp = e[1], fpp = 0.0f;
-#pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        const float xa = x - R.al[k];
-        const float b = R.be[k - 1];
-        float p2 = fmaf(xa, p1, -b * p0);
-        float d2 = fmaf(xa, d1, fmaf(-b, d0, p1));
-        float s2 = fmaf(xa, s1, fmaf(-b, s0, 2.0f * d1));
-        f = fmaf(e[k + 1], p2, f);
-        fp = fmaf(e[k + 1], d2, fp);
-        fpp = fmaf(e[k + 1], s2, fpp);
-        p0 = p1; p1 = p2; d0 = d1; d1 = d2; s0 = s1; s1 = s2;
-    }
+    float f, fp, fpp;
+    kernel_poly_d2(R, e, x, f, fp, fpp);
     return laguerre_step(x, f, fp, fpp, lo, hi, right);
 }
 
@@ -496,6 +506,87 @@ MB_HD float unpack_query(const float4 v, float y, QueryRec& q) {
     q.x[0] = v.y;
     q.x[1] = v.z;
     q.F = 0.0f;
+    return v.x;
+}
+
+// Bracket of root sv of a query with j Gauss nodes below it (1 <= j <= 3),
+// as bound_query solves them: the interior root in (z_1, z_2) first when
+// j == 2, then the outer root beyond z_1 (j <= 2) or z_4 (j == 3).
+MB_HD void root_bracket(const Recon& R, int j, int sv, float& lo, float& hi) {
+    const bool left = j <= 2;
+    const float zb = left ? R.z[0] : R.z[3];
+    const float far = left ? zb - R.span : zb + R.span;
+    const bool in = j == 2 && sv == 0;
+    lo = in ? R.z[0] : (left ? far : zb);
+    hi = in ? R.z[1] : (left ? zb : far);
+}
+
+// Compact kept query (8 bytes): {tau, bits}, bits = u_0 | u_1 << 13 | j << 26
+// | nroot << 29 with u_r the 13-bit position of root r in its bracket.
+constexpr int QPOS_BITS = 13;
+constexpr float QPOS_SCALE = 8192.0f;
+MB_HD float2 pack_query_compact(const Recon& R, float tau, const QueryRec& q) {
+    unsigned bits = ((unsigned)q.j << 26) | ((unsigned)q.nroot << 29);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (r < q.nroot) {
+            float lo, hi;
+            root_bracket(R, q.j, r, lo, hi);
+            const float u = (q.x[r] - lo) / (hi - lo);
+            const int code = (int)fminf(fmaxf(u * QPOS_SCALE, 0.0f), QPOS_SCALE - 1.0f);
+            bits |= (unsigned)code << (QPOS_BITS * r);
+        }
+    }
+    return make_float2(tau, int_bits_as_float((int)bits));
+}
+
+// One Laguerre step towards the nearest root (the larger denominator), for
+// polishing a root known to about 1e-4 of its bracket.
+MB_HD float laguerre_nearest_step(float x, float f, float fp, float fpp, float lo, float hi) {
+    const float v = fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 1e-30f);
+    const float q = v * rsqrt_(v);
+    const float xn = x - (f != 0.0f ? fdiv_(4.0f * f, fp + copysignf(q, fp)) : 0.0f);
+    return fminf(fmaxf(xn, lo), hi);
+}
+
+// Decodes a compact kept query at standardised y: each root from the centre
+// of its 13-bit bin (within 6e-5 of its bracket) by two Laguerre steps of the
+// kernel polynomial through the three-term recurrence (cubic convergence:
+// the same root as the solve, to rounding).
+MB_HD float unpack_query_compact(const Recon& R, float2 v, float y, QueryRec& q) {
+    const unsigned bits = (unsigned)float_bits_as_int(v.y);
+    q.y = y;
+    q.j = (int)((bits >> 26) & 7u);
+    q.nroot = (int)((bits >> 29) & 3u);
+    q.F = 0.0f;
+    q.x[0] = 0.0f;
+    q.x[1] = 0.0f;
+    if (q.nroot > 0) {
+        float P[5], e[5];
+        pis(R, y, P);
+        e[0] = 1.0f;
+#pragma unroll
+        for (int k = 1; k < 5; ++k) e[k] = R.h[k - 1] * P[k];
+        // the same scaling as the solve (roots are scale invariant)
+        const float sc = fdiv_(1.0f, fabsf(e[0]) + fabsf(e[1]) + fabsf(e[2]) + fabsf(e[3]) + fabsf(e[4]));
+#pragma unroll
+        for (int k = 0; k < 5; ++k) e[k] *= sc;
+#pragma unroll 1
+        for (int r = 0; r < q.nroot; ++r) {
+            float lo, hi;
+            root_bracket(R, q.j, r, lo, hi);
+            const unsigned code = (bits >> (QPOS_BITS * r)) & 8191u;
+            float x = fmaf(hi - lo, ((float)code + 0.5f) * (1.0f / QPOS_SCALE), lo);
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                float f, fp, fpp;
+                kernel_poly_d2(R, e, x, f, fp, fpp);
+                x = laguerre_nearest_step(x, f, fp, fpp, lo, hi);
+            }
+            if (r == 0) q.x[0] = x;
+            else q.x[1] = x;
+        }
+    }
     return v.x;
 }
 
@@ -663,25 +754,26 @@ namespace mb {
 // ----------------------------------------------------------------------------
 // Optical depth at warped depth gq of one sample: power-moment bounds (with
 // the query kept for the adjoint when qout != nullptr) or trigonometric ones.
-template <bool SAVE>
-MB_HD float sample_depth(const Params& p, const Recon& R, float gq, float4* qout) {
+template <bool SAVE, int QB = 16>
+MB_HD float sample_depth(const Params& p, const Recon& R, float gq, char* qout) {
     const float y = fmaf(2.0f, gq, -1.0f);
     if (SAVE && qout) {
         QueryRec q;
         const float tau = bound_query<true>(R, p.beta, y, &q);
-        *qout = pack_query(tau, q);
+        if (QB == 8) *reinterpret_cast<float2*>(qout) = pack_query_compact(R, tau, q);
+        else *reinterpret_cast<float4*>(qout) = pack_query(tau, q);
         return tau;
     }
     return optical_depth(R, p.beta, y);
 }
-template <bool SAVE>
-MB_HD float sample_depth(const Params& p, const TrigRecon& T, float gq, float4*) {
+template <bool SAVE, int QB = 16>
+MB_HD float sample_depth(const Params& p, const TrigRecon& T, float gq, char*) {
     return trig_optical_depth(p, T, gq);
 }
 
-template <int NI, bool SAVE = false, class RecT = Recon>
+template <int NI, bool SAVE = false, class RecT = Recon, int QB = 16>
 MB_HD float pair_quadrature(const Params& p, const RecT& R, const Gauss1D& g, float* pen,
-                            float4* __restrict__ qout = nullptr) {
+                            char* __restrict__ qout = nullptr) {
     // streamed over the samples (one copy of the bound-query code): interval
     // j-1 is accumulated once sample j is known
     const int N = NI > 0 ? NI : p.n_intervals;
@@ -696,7 +788,7 @@ MB_HD float pair_quadrature(const Params& p, const RecT& R, const Gauss1D& g, fl
     for (int j = 0; j <= N; ++j) {
         const float raw = fmaf(ks, p.x_nodes[j], g.mu);
         const float tj = fminf(fmaxf(raw, p.t_near), p.t_far);
-        const float tau = sample_depth<SAVE>(p, R, warp_only(p, tj), qout ? qout + j : nullptr);
+        const float tau = sample_depth<SAVE, QB>(p, R, warp_only(p, tj), qout ? qout + j * QB : nullptr);
         float erf_j = p.x_erf[j], gau_j = p.x_gau[j];
         if (tj != raw) {
             const float b = (tj - g.mu) * isq;

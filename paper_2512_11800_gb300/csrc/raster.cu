@@ -143,7 +143,7 @@ __device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, i
 #ifndef MB_SHADE_MIN_CTAS
 #define MB_SHADE_MIN_CTAS 3      // resident CTAs per SM the register budget is sized for
 #endif
-template <int NI, bool SAVE, class RecT>
+template <int NI, bool SAVE, class RecT, int QB = 16>
 __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                                                const int32_t* __restrict__ ids, const int2* __restrict__ ranges,
                                                int64_t P, int64_t npix, const StatusWords* sw,
@@ -151,13 +151,14 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                                                float* __restrict__ rgb,
                                                float* __restrict__ T_final, float* __restrict__ penalty,
                                                float* __restrict__ saved, const int* __restrict__ npp,
-                                               const long long* __restrict__ pq_off, float4* __restrict__ pq,
+                                               const long long* __restrict__ pq_off, char* __restrict__ pq,
                                                int64_t qcap, TableArgs ta) {
     extern __shared__ float4 s_raw[];
     float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
     const bool any = sw->n_valid != 0;
-    // saved queries: a pixel's pairs from pq_off[pix], N+1 float4 each, for
-    // the pixels all of whose pairs fit the capacity (a prefix in pixel order)
+    // saved queries: a pixel's pairs from pq_off[pix], N+1 queries of QB bytes
+    // each, for the pixels all of whose pairs fit the capacity (a prefix in
+    // pixel order)
     const int nq = (NI > 0 ? NI : p.n_intervals) + 1;
     int fp, fx0, fy0;
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
@@ -168,10 +169,10 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
         else R.m0 = 0.0f;
         float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, O = 0.0f, Pen = 0.0f;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
-        float4* qp = nullptr;
+        char* qp = nullptr;
         if (SAVE && c.inside) {
             const long long off = pq_off[c.pix];
-            if (off + npp[c.pix] <= qcap) qp = pq + (size_t)off * nq;
+            if (off + npp[c.pix] <= qcap) qp = pq + (size_t)off * nq * QB;
         }
         for (int pos = c.start; pos < c.end; pos += 32) {
             const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                     const float* r = s_buf + k * REC;
                     if (!rect_contains(r, c.px, c.py)) continue;
                     const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
-                    const float Oi = pair_quadrature<NI, SAVE, RecT>(p, R, g, &Pen, qp);
-                    if (SAVE && qp) qp += nq;
+                    const float Oi = pair_quadrature<NI, SAVE, RecT, QB>(p, R, g, &Pen, qp);
+                    if (SAVE && qp) qp += nq * QB;
                     S0 = fmaf(r[R_RGB + 0], Oi, S0);
                     S1 = fmaf(r[R_RGB + 1], Oi, S1);
                     S2 = fmaf(r[R_RGB + 2], Oi, S2);
@@ -256,6 +257,8 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
               : L.tab_m > 0
                     ? (p.n_intervals == 3 ? k_shade<3, false, TabPixel>
                        : p.n_intervals == 5 ? k_shade<5, false, TabPixel> : k_shade<0, false, TabPixel>)
+              : save && p.qbytes == 8
+                    ? (p.n_intervals == 3 ? k_shade<3, true, Recon, 8> : k_shade<0, true, Recon, 8>)
               : p.n_intervals == 3 ? (save ? k_shade<3, true, Recon> : k_shade<3, false, Recon>)
               : p.n_intervals == 5 ? (save ? k_shade<5, true, Recon> : k_shade<5, false, Recon>)
                                    : (save ? k_shade<0, true, Recon> : k_shade<0, false, Recon>);
@@ -268,7 +271,7 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
         ws + L.moments, rgb, T_final, penalty, reinterpret_cast<float*>(ws + L.saved),
         save ? reinterpret_cast<const int*>(ws + L.npp) : nullptr,
         save ? reinterpret_cast<const long long*>(ws + L.pq_off) : nullptr,
-        save ? reinterpret_cast<float4*>(ws + L.pq) : nullptr, L.qcap,
+        save ? ws + L.pq : nullptr, L.qcap,
         TableArgs{L.tab_m > 0 ? reinterpret_cast<const float2*>(ws + L.tab) : nullptr,
                   L.tab_m > 0 ? reinterpret_cast<const float*>(ws + L.tab_e) : nullptr, L.tab_m});
 }

@@ -129,8 +129,8 @@ MB_HD float table_depth(const TabPixel& T, float gq) {
     return fmaf(h00, k0.x, fmaf(h10 * h, k0.y, fmaf(h01, k1.x, h11 * h * k1.y)));
 }
 
-template <bool SAVE>
-MB_HD float sample_depth(const Params& p, const TabPixel& T, float gq, float4*) {
+template <bool SAVE, int QB = 16>
+MB_HD float sample_depth(const Params& p, const TabPixel& T, float gq, char*) {
     return table_depth(T, gq);
 }
 

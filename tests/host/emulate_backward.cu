@@ -8,8 +8,9 @@
 //   per record: expand_geometry, preprocess_bwd_one.
 // The per-record sums are plain host sums in place of the warp, shared-memory
 // and global reductions; binning, tiling and launches are left out.  With
-// argv[3] == "saved" the bound queries kept by the forward feed pass 1, else
-// pass 1 solves them again.  argv[4] (optional): N intervals (default 3; other
+// argv[3] == "saved" the bound queries kept by the forward feed pass 1
+// ("compact": kept in the 8-byte form and restored by pass 1), else pass 1
+// solves them again.  argv[4] (optional): N intervals (default 3; other
 // values run the runtime-N templates).  argv[5] (optional): moment basis (0
 // power, 1 trigonometric: trig_moments, reconstruct_trig, the trigonometric
 // pair_backward, trig_finish_adjoint and trig_moment_adjoint; queries are
@@ -52,7 +53,8 @@ static void rd(FILE* f, T* x, size_t n) {
 
 int main(int argc, char** argv) {
     if (argc < 4 || argc > 6) return 2;
-    const bool saved = strcmp(argv[3], "saved") == 0;
+    const bool compact = strcmp(argv[3], "compact") == 0;
+    const bool saved = compact || strcmp(argv[3], "saved") == 0;
     FILE* f = fopen(argv[1], "rb");
     if (!f) return 2;
     int64_t P;
@@ -119,13 +121,17 @@ int main(int argc, char** argv) {
         if (trig) reconstruct_trig(p, acc, TR);
         else reconstruct_pixel(p, acc, R);
         float S[3] = {0, 0, 0}, O = 0, Pen = 0;
-        std::vector<float4> qs(mine.size() * nq);
+        std::vector<float4> qs16(mine.size() * nq);   // 16 bytes a query (8 used when compact)
+        char* qs = reinterpret_cast<char*>(qs16.data());
+        const int QBY = compact ? 8 : 16;
         for (size_t k = 0; k < mine.size(); ++k) {
             const float* r = &rec[mine[k] * REC];
             const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], rl, r2);
             const float Oi = trig ? pair_quadrature<0, false, TrigRecon>(p, TR, g, &Pen)
-                             : p.n_intervals == 3 ? pair_quadrature<3, true>(p, R, g, &Pen, &qs[k * nq])
-                                                  : pair_quadrature<0, true>(p, R, g, &Pen, &qs[k * nq]);
+                             : compact ? (p.n_intervals == 3 ? pair_quadrature<3, true, Recon, 8>(p, R, g, &Pen, qs + k * nq * QBY)
+                                                             : pair_quadrature<0, true, Recon, 8>(p, R, g, &Pen, qs + k * nq * QBY))
+                             : p.n_intervals == 3 ? pair_quadrature<3, true>(p, R, g, &Pen, qs + k * nq * QBY)
+                                                  : pair_quadrature<0, true>(p, R, g, &Pen, qs + k * nq * QBY);
             for (int c = 0; c < 3; ++c) S[c] += r[R_RGB + c] * Oi;
             O += Oi;
         }
@@ -143,10 +149,12 @@ int main(int argc, char** argv) {
             if (trig)
                 po = pair_backward<0, false, TrigRecon>(p, TR, g, a, pa.gP, B);
             else if (p.n_intervals == 3)
-                po = saved ? pair_backward<3, true>(p, R, g, a, pa.gP, B, &qs[k * nq])
+                po = compact ? pair_backward<3, true, Recon, 8>(p, R, g, a, pa.gP, B, qs + k * nq * QBY)
+                   : saved ? pair_backward<3, true>(p, R, g, a, pa.gP, B, qs + k * nq * QBY)
                            : pair_backward<3, false>(p, R, g, a, pa.gP, B);
             else
-                po = saved ? pair_backward<0, true>(p, R, g, a, pa.gP, B, &qs[k * nq])
+                po = compact ? pair_backward<0, true, Recon, 8>(p, R, g, a, pa.gP, B, qs + k * nq * QBY)
+                   : saved ? pair_backward<0, true>(p, R, g, a, pa.gP, B, qs + k * nq * QBY)
                            : pair_backward<0, false>(p, R, g, a, pa.gP, B);
             float c[NK_QUAD];
             for (int f2 = 0; f2 < NK_QUAD; ++f2) c[f2] = 0.0f;

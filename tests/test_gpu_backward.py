@@ -267,3 +267,33 @@ def test_finite_differences_on_256_gaussians():
           "max", float(rel.max()), "worst (fd, gpu):", [(float(fd[i]), float(an[i])) for i in worst])
     assert n_ok >= 200
     assert np.median(rel) < 1e-3 and np.quantile(rel, 0.95) < 5e-3
+
+
+def test_compact_queries_match_full():
+    """Kept queries in the 8-byte form (roots as 13-bit bracket positions,
+    restored by two Laguerre steps in pass 1): the image is bit-identical and
+    the gradients agree with the 16-byte form to rounding, with all pairs and
+    with part of them kept."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11800_gb300 import RasterConfig, Rasterizer
+    sc, cam = scenes.workload("uniform2k_128")
+    g = G(sc)
+    rng = np.random.default_rng(9)
+    dr = torch.as_tensor(rng.normal(size=(cam.width * cam.height, 3)), dtype=torch.float32, device="cuda")
+    res = {}
+    for fmt in ["full", "compact"]:
+        R = Rasterizer(RasterConfig(bg=(0.1, 0.2, 0.3), query_format=fmt))
+        tp, pp = R.pair_counts(g, cam)
+        for name, qc in [("all", pp), ("half", pp // 2)]:
+            out = R.render(g, cam, capacity=tp, query_capacity=qc)
+            assert R.status()[0] == 0 and R.cfg_c.compact_queries == (fmt == "compact")
+            grads = R.backward(g, cam, tp, dr, query_capacity=qc)
+            torch.cuda.synchronize()
+            res[fmt, name] = (out["rgb"].clone(), {k: v.clone() for k, v in grads.items()})
+    for name in ["all", "half"]:
+        assert torch.equal(res["compact", name][0], res["full", name][0])
+        for k in NAMES:
+            a, b = res["compact", name][1][k], res["full", name][1][k]
+            assert float((a - b).norm() / b.norm().clamp_min(1e-30)) <= 1e-5, (name, k)
+            assert float((a - b).abs().max() / b.abs().max().clamp_min(1e-30)) <= 1e-4, (name, k)

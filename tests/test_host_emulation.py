@@ -177,7 +177,7 @@ def test_host_emulated_tabulated_transmittance(emulator, tmp_path, name):
 NAMES = ["means", "scales", "quats", "weights", "sh"]
 
 
-@pytest.mark.parametrize("mode", ["saved", "recomputed"])
+@pytest.mark.parametrize("mode", ["saved", "compact", "recomputed"])
 @pytest.mark.parametrize("name", ["uniform2k_full", "sh3_near_camera", "sh3_near_camera_N5", "sh3_near_camera_N1"])
 def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, name, mode):
     N = 5 if name.endswith("N5") else (1 if name.endswith("N1") else 3)
