@@ -521,27 +521,32 @@ MB_HD void root_bracket(const Recon& R, int j, int sv, float& lo, float& hi) {
     hi = in ? R.z[1] : (left ? zb : far);
 }
 
-// Compact kept query (8 bytes): {tau, bits}, bits = u_0 | u_1 << 13 | j << 26
-// | nroot << 29 with u_r the 13-bit position of root r in its bracket.
-constexpr int QPOS_BITS = 13;
-constexpr float QPOS_SCALE = 8192.0f;
+// Compact kept query (8 bytes): {tau, bits}, bits = u_0 | u_1 << 16 with u_r
+// the 16-bit position of root r in its bracket (QPOS_NONE: no outer root).
+// The number j of Gauss nodes below y is not stored: the adjoint recomputes
+// y with the same operations, so the same j; the interior root (j == 2) is
+// root 0 and always present.
+constexpr unsigned QPOS_NONE = 0xFFFFu;
+constexpr float QPOS_SCALE = 65535.0f;
+#ifndef MB_QPOS_POLISH
+#define MB_QPOS_POLISH 1
+#endif
 MB_HD float2 pack_query_compact(const Recon& R, float tau, const QueryRec& q) {
-    unsigned bits = ((unsigned)q.j << 26) | ((unsigned)q.nroot << 29);
+    unsigned code[2] = {QPOS_NONE, QPOS_NONE};
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         if (r < q.nroot) {
             float lo, hi;
             root_bracket(R, q.j, r, lo, hi);
             const float u = (q.x[r] - lo) / (hi - lo);
-            const int code = (int)fminf(fmaxf(u * QPOS_SCALE, 0.0f), QPOS_SCALE - 1.0f);
-            bits |= (unsigned)code << (QPOS_BITS * r);
+            code[r] = (unsigned)fminf(fmaxf(u * QPOS_SCALE + 0.5f, 0.0f), QPOS_SCALE - 1.0f);
         }
     }
-    return make_float2(tau, int_bits_as_float((int)bits));
+    return make_float2(tau, int_bits_as_float((int)(code[0] | (code[1] << 16))));
 }
 
 // One Laguerre step towards the nearest root (the larger denominator), for
-// polishing a root known to about 1e-4 of its bracket.
+// polishing a root known to a few 1e-6 of its bracket.
 MB_HD float laguerre_nearest_step(float x, float f, float fp, float fpp, float lo, float hi) {
     const float v = fmaxf(3.0f * fmaf(3.0f * fp, fp, -4.0f * f * fpp), 1e-30f);
     const float q = v * rsqrt_(v);
@@ -549,20 +554,24 @@ MB_HD float laguerre_nearest_step(float x, float f, float fp, float fpp, float l
     return fminf(fmaxf(xn, lo), hi);
 }
 
-// Decodes a compact kept query at standardised y: each root from the centre
-// of its 13-bit bin (within 6e-5 of its bracket) by two Laguerre steps of the
-// kernel polynomial through the three-term recurrence (cubic convergence:
-// the same root as the solve, to rounding).
+// Decodes a compact kept query at standardised y: j from y, each root from
+// its 16-bit position (within 8e-6 of its bracket), polished by MB_QPOS_POLISH
+// Laguerre steps of the kernel polynomial through the three-term recurrence.
 MB_HD float unpack_query_compact(const Recon& R, float2 v, float y, QueryRec& q) {
     const unsigned bits = (unsigned)float_bits_as_int(v.y);
     q.y = y;
-    q.j = (int)((bits >> 26) & 7u);
-    q.nroot = (int)((bits >> 29) & 3u);
+    q.j = (R.z[0] < y) + (R.z[1] < y) + (R.z[2] < y) + (R.z[3] < y);
     q.F = 0.0f;
     q.x[0] = 0.0f;
     q.x[1] = 0.0f;
+    const unsigned c0 = bits & 0xFFFFu, c1 = bits >> 16;
+    // slot 0: the interior root (j == 2, always) or the outer one (j = 1, 3)
+    q.nroot = (q.j >= 1 && q.j <= 3 && c0 != QPOS_NONE) ? 1 + (q.j == 2 && c1 != QPOS_NONE) : 0;
+    if (R.m0 <= 0.0f) q.nroot = 0;
+#if MB_QPOS_POLISH > 0
+    float e[5];
     if (q.nroot > 0) {
-        float P[5], e[5];
+        float P[5];
         pis(R, y, P);
         e[0] = 1.0f;
 #pragma unroll
@@ -571,21 +580,23 @@ MB_HD float unpack_query_compact(const Recon& R, float2 v, float y, QueryRec& q)
         const float sc = fdiv_(1.0f, fabsf(e[0]) + fabsf(e[1]) + fabsf(e[2]) + fabsf(e[3]) + fabsf(e[4]));
 #pragma unroll
         for (int k = 0; k < 5; ++k) e[k] *= sc;
+    }
+#endif
 #pragma unroll 1
-        for (int r = 0; r < q.nroot; ++r) {
-            float lo, hi;
-            root_bracket(R, q.j, r, lo, hi);
-            const unsigned code = (bits >> (QPOS_BITS * r)) & 8191u;
-            float x = fmaf(hi - lo, ((float)code + 0.5f) * (1.0f / QPOS_SCALE), lo);
+    for (int r = 0; r < q.nroot; ++r) {
+        float lo, hi;
+        root_bracket(R, q.j, r, lo, hi);
+        float x = fmaf(hi - lo, (float)(r == 0 ? c0 : c1) * (1.0f / QPOS_SCALE), lo);
+#if MB_QPOS_POLISH > 0
 #pragma unroll
-            for (int it = 0; it < 2; ++it) {
-                float f, fp, fpp;
-                kernel_poly_d2(R, e, x, f, fp, fpp);
-                x = laguerre_nearest_step(x, f, fp, fpp, lo, hi);
-            }
-            if (r == 0) q.x[0] = x;
-            else q.x[1] = x;
+        for (int it = 0; it < MB_QPOS_POLISH; ++it) {
+            float f, fp, fpp;
+            kernel_poly_d2(R, e, x, f, fp, fpp);
+            x = laguerre_nearest_step(x, f, fp, fpp, lo, hi);
         }
+#endif
+        if (r == 0) q.x[0] = x;
+        else q.x[1] = x;
     }
     return v.x;
 }
