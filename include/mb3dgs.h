@@ -123,11 +123,13 @@ typedef struct mb3dgs_config {
                            differentiate the solved bounds that the table approximates
                            (pass 1 solves its queries again; query_capacity is ignored). */
     int compact_queries; /* 0 (default): a kept bound query takes 16 bytes {tau, x_0, x_1,
-                           j | nroot}.  1: 8 bytes {tau, the roots as 13-bit positions in
-                           their brackets, j, nroot}; the backward restores each root by
-                           two Laguerre steps from its position (the results agree with
-                           the 16-byte form to rounding), so twice as many pairs keep
-                           their queries in the same memory. */
+                           j | nroot}.  1: 8 bytes {tau, the roots as 16-bit positions in
+                           their brackets}; the backward recomputes j from the query
+                           (the same operations give the same value) and restores each
+                           root by one Laguerre step from its position (the gradients
+                           agree with the 16-byte form to rounding), so twice as many
+                           pairs keep their queries in the same memory, at some cost in
+                           the backward. */
 } mb3dgs_config;
 
 /* Device pointers, caller-owned, layout as in the file comment. */

@@ -44,10 +44,12 @@ class RasterConfig:
     # (64 B per (pixel, Gaussian) pair at N = 3); False: backward recomputes them
     save_queries: bool = True
     query_budget_gb: float = 48.0  # device memory for kept queries; pixels beyond it recompute theirs
-    # kept-query form: "full" (16 B a query), "compact" (8 B: roots as 13-bit
-    # positions, restored by two Laguerre steps in the backward), or "auto":
-    # full when all of the frame's queries fit the budget, compact otherwise
-    query_format: str = "auto"
+    # kept-query form: "full" (16 B a query) or "compact" (8 B: roots as 16-bit
+    # positions in their brackets, restored by one Laguerre step in the
+    # backward; twice the pairs in the same memory, but the restore costs more
+    # than solving the remaining pixels' queries again at the 16-view frame's
+    # 57 % kept fraction)
+    query_format: str = "full"
     # execution shape (results do not depend on it; Rasterizer.autotune sets it)
     tile_w: int = 16
     tile_h: int = 16
@@ -236,9 +238,9 @@ class Rasterizer:
         nq = self.config.n_intervals + 1
         room = int(self.config.query_budget_gb * 2 ** 30)
         fmt = self.config.query_format
-        if fmt not in ("auto", "full", "compact"):
-            raise ValueError("query_format must be auto, full or compact")
-        compact = fmt == "compact" or (fmt == "auto" and n * 16 * nq > room)
+        if fmt not in ("full", "compact"):
+            raise ValueError("query_format must be full or compact")
+        compact = fmt == "compact"
         self.cfg_c.compact_queries = 1 if compact else 0
         budget = room // ((8 if compact else 16) * nq)
         keep = self.config.save_queries and self.config.basis == "power" and not self.config.tau_table

@@ -105,10 +105,8 @@ def test_execution_shape_validation_and_tile_counts(lib):
 def test_query_capacity_policy():
     """Query slots (16 B x (N+1) a pair, 8 B x (N+1) in the compact form): all
     of the frame's pairs while they fit the budget, else as many as the
-    budget holds (the backward solves the other pixels' queries again); the
-    automatic form is the 16-byte one while the whole frame fits, else the
-    compact one.  None without saved queries or with the trigonometric
-    basis.  The C layout accepts capacities beyond 2^31."""
+    budget holds (the backward solves the other pixels' queries again).  None
+    without saved queries or with the trigonometric basis.  The C layout accepts capacities beyond 2^31."""
     from paper_2512_11800_gb300 import RasterConfig, Rasterizer
     from paper_2512_11800_gb300 import _binding as B
     R = Rasterizer(RasterConfig(query_budget_gb=1.0, query_format="full"))
@@ -118,14 +116,13 @@ def test_query_capacity_policy():
     assert R.set_query_capacity(fit + 1) == fit
     assert R.set_query_capacity(10 * fit) == fit and R.cfg_c.compact_queries == 0
     assert R.set_query_capacity(0) == 0
-    R.config.query_format = "auto"
-    assert R.set_query_capacity(fit) == fit and R.cfg_c.compact_queries == 0
-    assert R.set_query_capacity(fit + 1) == fit + 1 and R.cfg_c.compact_queries == 1
-    assert R.set_query_capacity(10 * fit) == 2 * fit and R.cfg_c.compact_queries == 1
     R.config.query_format = "compact"
     assert R.set_query_capacity(fit) == fit and R.cfg_c.compact_queries == 1
+    assert R.set_query_capacity(fit + 1) == fit + 1
+    assert R.set_query_capacity(10 * fit) == 2 * fit and R.cfg_c.compact_queries == 1
     n8, n16 = C.c_size_t(0), C.c_size_t(0)
     cam = _cam(128, 128)
+    R.set_query_capacity(fit)                            # the same slots in both forms
     assert R.lib.mb3dgs_workspace_size(C.byref(R.cfg_c), C.byref(cam), 1, 100, 0, C.byref(n8)) == 0
     R.config.query_format = "full"
     R.set_query_capacity(fit)
