@@ -61,8 +61,8 @@ enum { MB3DGS_MOMENTS_F32 = 0, MB3DGS_MOMENTS_BF16 = 1, MB3DGS_MOMENTS_F16 = 2 }
  * Eq. 10-12) with the bounds of Eq. 8.  TRIG: trigonometric moments (Sec. 3.2,
  * Eq. 13-14; App. C) of the angle (2 pi - theta) g-hat, with the bounds of the
  * Gauss-Szego rule on the unit circle cut in the middle of the wrapping zone.
- * Both bases have the adjoint calls (the TRIG adjoint solves its bound
- * queries again in pass 1: query_capacity is ignored). */
+ * Both bases have the adjoint calls and keep their bound queries as
+ * query_capacity says. */
 enum { MB3DGS_BASIS_POWER = 0, MB3DGS_BASIS_TRIG = 1 };
 /* How the per-tile passes map tiles of all views to CTAs.  QUEUE: one wave of
  * persistent CTAs takes tiles from an atomic queue in decreasing order of
@@ -110,7 +110,8 @@ typedef struct mb3dgs_config {
                            caller sets; the results are the same).  0 (default):
                            all are recomputed; the pixel-pair count of
                            mb3dgs_get_pair_counts keeps all.  Below 2^40.
-                           Ignored with the TRIG basis. */
+                           TRIG: {tau, node angles x_0, x_1, j | ns} in 16 bytes.
+                           Ignored with a table (tau_table). */
     int basis;          /* MB3DGS_BASIS_*; default POWER */
     float trig_theta;   /* TRIG: wrapping angle theta in (0, 2 pi) (reading); pi/2 */
     int tau_table;      /* POWER: 0 (default) solves every bound query of the quadrature
@@ -129,7 +130,7 @@ typedef struct mb3dgs_config {
                            root by one Laguerre step from its position (the gradients
                            agree with the 16-byte form to rounding), so twice as many
                            pairs keep their queries in the same memory, at some cost in
-                           the backward. */
+                           the backward.  POWER only (MB3DGS_ERR_UNSUPPORTED otherwise). */
 } mb3dgs_config;
 
 /* Device pointers, caller-owned, layout as in the file comment. */

@@ -240,10 +240,10 @@ class Rasterizer:
         fmt = self.config.query_format
         if fmt not in ("full", "compact"):
             raise ValueError("query_format must be full or compact")
-        compact = fmt == "compact"
+        compact = fmt == "compact" and self.config.basis == "power"
         self.cfg_c.compact_queries = 1 if compact else 0
         budget = room // ((8 if compact else 16) * nq)
-        keep = self.config.save_queries and self.config.basis == "power" and not self.config.tau_table
+        keep = self.config.save_queries and not self.config.tau_table
         self.cfg_c.query_capacity = min(n, budget) if keep else 0
         return int(self.cfg_c.query_capacity)
 

@@ -60,6 +60,7 @@ static int check_cfg(const mb3dgs_config* c) {
         return MB3DGS_ERR_INVALID_ARG;
     if (c->tau_table != 0 && (c->tau_table < 8 || c->tau_table > 128)) return MB3DGS_ERR_INVALID_ARG;
     if (c->compact_queries != 0 && c->compact_queries != 1) return MB3DGS_ERR_INVALID_ARG;
+    if (c->compact_queries && c->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;   // power-moment roots only
     if (c->tau_table != 0 && c->basis != MB3DGS_BASIS_POWER) return MB3DGS_ERR_UNSUPPORTED;
     if (c->tile_w != 0 || c->tile_h != 0) {
         const int tw = c->tile_w, th = c->tile_h;
@@ -124,7 +125,7 @@ static int make_layout(const mb3dgs_config* cfg, const ViewTable& vt, int64_t np
     while ((int64_t(1) << bits) < ntiles) ++bits;
     L.sort_passes = (bits + 7) / 8;
     L.final_buf = L.sort_passes % 2;
-    L.qcap = cfg && cfg->basis == MB3DGS_BASIS_POWER ? cfg->query_capacity : 0;
+    L.qcap = cfg && cfg->tau_table == 0 ? cfg->query_capacity : 0;
     if (L.qcap < 0 || L.qcap >= (int64_t(1) << 40)) return MB3DGS_ERR_INVALID_ARG;
     L.scan_tmp_elems = std::max(scan_tmp_elems(L.VP), scan_tmp_elems((int64_t)256 * L.nb_sort));
     if (L.qcap > 0) L.scan_tmp_elems = std::max(L.scan_tmp_elems, 2 * scan_tmp_elems(npix));   // 64-bit scan

@@ -409,9 +409,12 @@ int launch_backward_quadrature(const Params& p, const ViewTable& vt, const Layou
     for (int pass = kept ? 0 : 1; pass < 2; ++pass) {
         const bool saved_q = pass == 0;
         auto k1 = p.basis == MB3DGS_BASIS_TRIG
-                      ? (p.n_intervals == 3   ? k_bwd_quadrature<3, false, TrigRecon>
-                         : p.n_intervals == 5 ? k_bwd_quadrature<5, false, TrigRecon>
-                                              : k_bwd_quadrature<0, false, TrigRecon>)
+                      ? (saved_q ? (p.n_intervals == 3   ? k_bwd_quadrature<3, true, TrigRecon>
+                                    : p.n_intervals == 5 ? k_bwd_quadrature<5, true, TrigRecon>
+                                                         : k_bwd_quadrature<0, true, TrigRecon>)
+                                 : (p.n_intervals == 3   ? k_bwd_quadrature<3, false, TrigRecon>
+                                    : p.n_intervals == 5 ? k_bwd_quadrature<5, false, TrigRecon>
+                                                         : k_bwd_quadrature<0, false, TrigRecon>))
                   : saved_q && p.qbytes == 8
                       ? (p.n_intervals == 3 ? k_bwd_quadrature<3, true, Recon, 8> : k_bwd_quadrature<0, true, Recon, 8>)
                   : p.n_intervals == 3 ? (saved_q ? k_bwd_quadrature<3, true, Recon> : k_bwd_quadrature<3, false, Recon>)

@@ -231,7 +231,8 @@ MB_HD float sample_query(const Params& p, const Recon& R, float gj, float4 qv, Q
     return bound_query<true>(R, p.beta, fmaf(2.0f, gj, -1.0f), &q);
 }
 template <bool SAVED, int QB>
-MB_HD float sample_query(const Params& p, const TrigRecon& T, float gj, float4, TrigQueryRec& q) {
+MB_HD float sample_query(const Params& p, const TrigRecon& T, float gj, float4 qv, TrigQueryRec& q) {
+    if (SAVED) return unpack_trig_query(p, qv, gj, q);
     return trig_bound_query<true>(p, T, gj, &q);
 }
 

@@ -778,7 +778,13 @@ MB_HD float sample_depth(const Params& p, const Recon& R, float gq, char* qout) 
     return optical_depth(R, p.beta, y);
 }
 template <bool SAVE, int QB = 16>
-MB_HD float sample_depth(const Params& p, const TrigRecon& T, float gq, char*) {
+MB_HD float sample_depth(const Params& p, const TrigRecon& T, float gq, char* qout) {
+    if (SAVE && qout) {
+        TrigQueryRec q;
+        const float tau = trig_bound_query<true>(p, T, gq, &q);
+        *reinterpret_cast<float4*>(qout) = pack_trig_query(tau, q);
+        return tau;
+    }
     return trig_optical_depth(p, T, gq);
 }
 

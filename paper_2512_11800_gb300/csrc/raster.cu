@@ -252,8 +252,10 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
     const size_t smem = sizeof(float) * WARP_STAGE_FLOATS * WARPS;
     const bool save = L.qcap > 0;
     auto kern = p.basis == MB3DGS_BASIS_TRIG
-                    ? (p.n_intervals == 3 ? k_shade<3, false, TrigRecon>
-                       : p.n_intervals == 5 ? k_shade<5, false, TrigRecon> : k_shade<0, false, TrigRecon>)
+                    ? (save ? (p.n_intervals == 3   ? k_shade<3, true, TrigRecon>
+                               : p.n_intervals == 5 ? k_shade<5, true, TrigRecon> : k_shade<0, true, TrigRecon>)
+                            : (p.n_intervals == 3   ? k_shade<3, false, TrigRecon>
+                               : p.n_intervals == 5 ? k_shade<5, false, TrigRecon> : k_shade<0, false, TrigRecon>))
               : L.tab_m > 0
                     ? (p.n_intervals == 3 ? k_shade<3, false, TabPixel>
                        : p.n_intervals == 5 ? k_shade<5, false, TabPixel> : k_shade<0, false, TabPixel>)

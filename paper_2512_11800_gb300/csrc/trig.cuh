@@ -201,6 +201,23 @@ MB_HD float trig_optical_depth(const Params& p, const TrigRecon& T, float gq) {
     return trig_bound_query<false>(p, T, gq, nullptr);
 }
 
+// A trigonometric bound query kept for the adjoint (16 bytes):
+// {tau, x_0, x_1, j | ns << 4}; psi_w and `inside` follow from the warped
+// depth, which the adjoint forms with the same operations.
+MB_HD float4 pack_trig_query(float tau, const TrigQueryRec& q) {
+    return make_float4(tau, q.x[0], q.x[1], int_bits_as_float(q.j | (q.ns << 4)));
+}
+MB_HD float unpack_trig_query(const Params& p, float4 v, float gq, TrigQueryRec& q) {
+    const int m = float_bits_as_int(v.w);
+    q.psi = p.trig_A * fminf(fmaxf(gq, 0.0f), 1.0f);
+    q.inside = gq > 0.0f && gq < 1.0f;
+    q.j = m & 15;
+    q.ns = m >> 4;
+    q.x[0] = v.y;
+    q.x[1] = v.z;
+    return v.x;
+}
+
 // Levinson-Durbin recursion of one attempt, with the states the adjoint
 // re-traces: the monic Szego polynomials Phi_k (coefficients P[k][0..k]),
 // their norms E_k, the numerators n_k = <1, z Phi_k> and g_k = n_k / E_k =

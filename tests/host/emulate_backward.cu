@@ -13,8 +13,8 @@
 // solves them again.  argv[4] (optional): N intervals (default 3; other
 // values run the runtime-N templates).  argv[5] (optional): moment basis (0
 // power, 1 trigonometric: trig_moments, reconstruct_trig, the trigonometric
-// pair_backward, trig_finish_adjoint and trig_moment_adjoint; queries are
-// always solved again).
+// pair_backward, trig_finish_adjoint and trig_moment_adjoint; "saved" keeps
+// their queries in the 16-byte trigonometric form).
 //
 // argv[1]: input file (as for emulate_forward, then float32 dL/drgb [h][w][3]
 // and dL/dP [h][w] of the region); argv[2]: output file (float32 gradients of
@@ -127,7 +127,8 @@ int main(int argc, char** argv) {
         for (size_t k = 0; k < mine.size(); ++k) {
             const float* r = &rec[mine[k] * REC];
             const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], rl, r2);
-            const float Oi = trig ? pair_quadrature<0, false, TrigRecon>(p, TR, g, &Pen)
+            const float Oi = trig ? (saved ? pair_quadrature<0, true, TrigRecon>(p, TR, g, &Pen, qs + k * nq * 16)
+                                           : pair_quadrature<0, false, TrigRecon>(p, TR, g, &Pen))
                              : compact ? (p.n_intervals == 3 ? pair_quadrature<3, true, Recon, 8>(p, R, g, &Pen, qs + k * nq * QBY)
                                                              : pair_quadrature<0, true, Recon, 8>(p, R, g, &Pen, qs + k * nq * QBY))
                              : p.n_intervals == 3 ? pair_quadrature<3, true>(p, R, g, &Pen, qs + k * nq * QBY)
@@ -147,7 +148,8 @@ int main(int argc, char** argv) {
             const float a = pa.gS[0] * r[R_RGB] + pa.gS[1] * r[R_RGB + 1] + pa.gS[2] * r[R_RGB + 2] + pa.gO;
             PairOut po;
             if (trig)
-                po = pair_backward<0, false, TrigRecon>(p, TR, g, a, pa.gP, B);
+                po = saved ? pair_backward<0, true, TrigRecon>(p, TR, g, a, pa.gP, B, qs + k * nq * 16)
+                           : pair_backward<0, false, TrigRecon>(p, TR, g, a, pa.gP, B);
             else if (p.n_intervals == 3)
                 po = compact ? pair_backward<3, true, Recon, 8>(p, R, g, a, pa.gP, B, qs + k * nq * QBY)
                    : saved ? pair_backward<3, true>(p, R, g, a, pa.gP, B, qs + k * nq * QBY)

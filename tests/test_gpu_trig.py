@@ -190,3 +190,28 @@ def test_trig_backward_full_size_crop():
     err = _rel_errors(gg, ref)
     print("trig backward shells1M crop N=5", err, "pairs", ref["out"]["n_pairs"])
     assert max(err.values()) <= REL, err
+
+
+def test_trig_kept_queries_match_solved():
+    """Trigonometric bound queries kept by the quadrature pass (16 bytes:
+    tau, the node angles, j and the node count) for all, half or none of the
+    pairs: the image is bit-identical and the gradients equal those of
+    queries solved again in pass 1 to rounding."""
+    R = _rasterizer(5, bg=(0.1, 0.2, 0.3))
+    sc, cam = scenes.workload("uniform2k_128")
+    g = G(sc)
+    tp, pp = R.pair_counts(g, cam)
+    rng = np.random.default_rng(11)
+    dr = torch.as_tensor(rng.normal(size=(cam.width * cam.height, 3)), dtype=torch.float32, device="cuda")
+    res = {}
+    for name, qc in [("all", pp), ("half", pp // 2), ("none", 0)]:
+        out = R.render(g, cam, capacity=tp, query_capacity=qc)
+        assert R.status()[0] == 0 and R.cfg_c.query_capacity == qc
+        grads = R.backward(g, cam, tp, dr, query_capacity=qc)
+        torch.cuda.synchronize()
+        res[name] = (out["rgb"].clone(), {k: v.clone() for k, v in grads.items()})
+    for name in ["all", "half"]:
+        assert torch.equal(res[name][0], res["none"][0])
+        for k in NAMES:
+            a, b = res[name][1][k], res["none"][1][k]
+            assert float((a - b).norm() / b.norm().clamp_min(1e-30)) <= 1e-5, (name, k)

@@ -207,8 +207,9 @@ def test_host_emulated_backward_matches_oracle_gradient(emulator_bwd, tmp_path, 
     assert max(err.values()) <= 1e-3, (name, mode, err)
 
 
+@pytest.mark.parametrize("mode", ["saved", "recomputed"])
 @pytest.mark.parametrize("N", [3, 5])
-def test_host_emulated_trig_backward_matches_oracle_gradient(emulator_bwd, tmp_path, N):
+def test_host_emulated_trig_backward_matches_oracle_gradient(emulator_bwd, tmp_path, N, mode):
     """The trigonometric adjoint (Verblunsky-coefficient query adjoints,
     reverse Levinson-Durbin, the reverse of Eq. 14) against the oracle's
     autograd gradient through its trigonometric bounds."""
@@ -220,7 +221,7 @@ def test_host_emulated_trig_backward_matches_oracle_gradient(emulator_bwd, tmp_p
     gP_img = rng.normal(size=(cam.height, cam.width)) * 0.1
     fin, fout = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     _write_input(fin, sc, cam, region, extra=(g_img, gP_img))
-    subprocess.run([emulator_bwd, fin, fout, "recomputed", str(N), "1"], check=True, timeout=900)
+    subprocess.run([emulator_bwd, fin, fout, mode, str(N), "1"], check=True, timeout=900)
     d = np.fromfile(fout, np.float32).astype(np.float64)
     shapes = [sc.means.shape, sc.scales.shape, sc.quats.shape, sc.weights.shape, sc.sh.shape]
     got, o = {}, 0
@@ -231,7 +232,7 @@ def test_host_emulated_trig_backward_matches_oracle_gradient(emulator_bwd, tmp_p
     ref = O.render_grad(sc, cam, oracle_config(n_intervals=N, basis="trig"), g_img, gP_img)
     err = {k: float(np.linalg.norm(got[k] - ref[k].reshape(-1)) / max(np.linalg.norm(ref[k]), 1e-30)) for k in NAMES}
     emax = {k: float(np.abs(got[k] - ref[k].reshape(-1)).max() / max(np.abs(ref[k]).max(), 1e-30)) for k in NAMES}
-    print("host-emulated trig backward N=%d rel-L2" % N, {k: "%.2e" % v for k, v in err.items()},
+    print("host-emulated trig backward N=%d %s rel-L2" % (N, mode), {k: "%.2e" % v for k, v in err.items()},
           "max/max", {k: "%.2e" % v for k, v in emax.items()})
     assert max(err.values()) <= 1e-3 and max(emax.values()) <= 1e-3, (N, err, emax)
 
