@@ -106,7 +106,8 @@ def test_query_capacity_policy():
     """Query slots (16 B x (N+1) a pair, 8 B x (N+1) in the compact form): all
     of the frame's pairs while they fit the budget, else as many as the
     budget holds (the backward solves the other pixels' queries again).  None
-    without saved queries or with the trigonometric basis.  The C layout accepts capacities beyond 2^31."""
+    without saved queries or with a table; the trigonometric basis keeps the
+    16-byte form.  The C layout accepts capacities beyond 2^31."""
     from paper_2512_11800_gb300 import RasterConfig, Rasterizer
     from paper_2512_11800_gb300 import _binding as B
     R = Rasterizer(RasterConfig(query_budget_gb=1.0, query_format="full"))
@@ -136,8 +137,10 @@ def test_query_capacity_policy():
     assert n.value >= 2 ** 33 * per_pair
     R.config.save_queries = False
     assert R.set_query_capacity(1000) == 0
-    Rt = Rasterizer(RasterConfig(basis="trig"))
-    assert Rt.set_query_capacity(1000) == 0
+    Rt = Rasterizer(RasterConfig(basis="trig", query_format="compact"))
+    assert Rt.set_query_capacity(1000) == 1000 and Rt.cfg_c.compact_queries == 0   # 16-byte trig queries
+    Rtab = Rasterizer(RasterConfig(tau_table=48))
+    assert Rtab.set_query_capacity(1000) == 0
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
