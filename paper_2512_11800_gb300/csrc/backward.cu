@@ -454,8 +454,8 @@ int launch_backward_moments(const Params& p, const ViewTable& vt, const Layout& 
 // Chain rule through the preprocessing to the Gaussian parameters.
 int launch_backward_preprocess(const Params& p, const ViewTable& vt, const Layout& L, char* ws,
                                const mb3dgs_gaussians& g, const mb3dgs_gaussian_grads& gr, cudaStream_t st) {
-    if (!gr.means || !gr.scales || !gr.quats || !gr.weights || !gr.sh) return MB3DGS_ERR_INVALID_ARG;
     if (L.P == 0) return MB3DGS_OK;
+    if (!gr.means || !gr.scales || !gr.quats || !gr.weights || !gr.sh) return MB3DGS_ERR_INVALID_ARG;
     count_launch();
     k_preprocess_bwd<<<(unsigned)ceil_div64(L.P, 64), 64, 0, st>>>(
         p, vt, g.means, g.scales, g.quats, g.weights, g.sh, L.P, g.sh_degree,

@@ -134,6 +134,10 @@ def test_densify_edge_cases():
     # everything pruned: an empty set
     got, action, first = _run(sc, A.ADCConfig(prune_opacity=float(np.float32(0.999999))), abs_sum, count)
     assert len(got["weights"]) == 0 and np.all(first == 0)
+    # no Gaussians at all
+    none = scenes.scene_uniform(0, 24)
+    got, action, first = _run(none, A.ADCConfig(), np.zeros((0, 3), np.float32), np.zeros(0, np.int32))
+    assert len(got["weights"]) == 0 and len(action) == 0
     # everything cloned, everything split
     ones = np.ones((sc.P, 3), np.float32)
     cnt = np.ones(sc.P, np.int32)

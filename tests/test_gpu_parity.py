@@ -154,6 +154,18 @@ def test_empty_and_culled_scenes(R):
     behind.means[:, 2] = -10.0                        # all behind the camera
     out = Rb.render(G(behind), cam)
     assert out["capacity"] == 0 and torch.all(out["T"] == 1.0)
+    # the adjoint of an empty frame: zero gradients, both bases
+    for basis in ["power", "trig"]:
+        Rx = Rasterizer(RasterConfig(bg=(0.25, 0.5, 0.75), basis=basis))
+        for sc in [empty, behind]:
+            g = G(sc)
+            out = Rx.render(g, cam)
+            grads = Rx.backward(g, cam, out["capacity"], torch.ones_like(out["rgb"]), torch.ones_like(out["T"]),
+                                dL_dT=torch.ones_like(out["T"]))
+            torch.cuda.synchronize()
+            assert Rx.status()[0] == 0
+            for k, v in grads.items():
+                assert v.numel() == 0 or torch.all(v == 0.0), (basis, k)
 
 
 def test_capacity_overflow_is_reported(R):
