@@ -169,17 +169,38 @@ __global__ void k_densify_write(AdcParams a, mb3dgs_gaussians g, const float* __
     }
     const int K3 = 3 * (g.sh_degree + 1) * (g.sh_degree + 1);
     unsigned todo = __ballot_sync(0xffffffffu, nres > 0);
+    // four inputs at a time: their loads are issued before their stores
+    constexpr int G = 4, MAXC = 2;   // K3 <= 48 <= MAXC x 32 floats a lane covers (8 measured slower)
     while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const long long si = __shfl_sync(0xffffffffu, (long long)i, src);
-        const long long so = __shfl_sync(0xffffffffu, (long long)o, src);
-        const int n = __shfl_sync(0xffffffffu, nres, src);
-        for (int c = lane; c < K3; c += 32) {
-            const float x = g.sh[(size_t)si * K3 + c];
-            out.sh[(size_t)so * K3 + c] = x;
-            if (n == 2) out.sh[(size_t)(so + 1) * K3 + c] = x;
+        long long si[G], so[G];
+        int n[G];
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            const int src = todo ? __ffs(todo) - 1 : 0;
+            const bool has = todo != 0;
+            todo &= todo - 1;
+            si[u] = __shfl_sync(0xffffffffu, (long long)i, src);
+            so[u] = __shfl_sync(0xffffffffu, (long long)o, src);
+            n[u] = has ? __shfl_sync(0xffffffffu, nres, src) : 0;
         }
+        float x[G][MAXC];
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+#pragma unroll
+            for (int t = 0; t < MAXC; ++t) {
+                const int c = lane + 32 * t;
+                x[u][t] = (n[u] > 0 && c < K3) ? g.sh[(size_t)si[u] * K3 + c] : 0.0f;
+            }
+#pragma unroll
+        for (int u = 0; u < G; ++u)
+#pragma unroll
+            for (int t = 0; t < MAXC; ++t) {
+                const int c = lane + 32 * t;
+                if (n[u] > 0 && c < K3) {
+                    out.sh[(size_t)so[u] * K3 + c] = x[u][t];
+                    if (n[u] == 2) out.sh[(size_t)(so[u] + 1) * K3 + c] = x[u][t];
+                }
+            }
     }
 }
 
