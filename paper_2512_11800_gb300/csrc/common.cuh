@@ -398,6 +398,18 @@ struct QueryRec {
     float F;        // (1 - beta) L + beta U
 };
 
+// Bracket of root sv of a query with j Gauss nodes below it (1 <= j <= 3),
+// as bound_query solves them: the interior root in (z_1, z_2) first when
+// j == 2, then the outer root beyond z_1 (j <= 2) or z_4 (j == 3).
+MB_HD void root_bracket(const Recon& R, int j, int sv, float& lo, float& hi) {
+    const bool left = j <= 2;
+    const float zb = left ? R.z[0] : R.z[3];
+    const float far = left ? zb - R.span : zb + R.span;
+    const bool in = j == 2 && sv == 0;
+    lo = in ? R.z[0] : (left ? far : zb);
+    hi = in ? R.z[1] : (left ? zb : far);
+}
+
 // tau(eta) = m0 ((1 - beta) L + beta U) = m0 (L + beta w0) at warped depth
 // y = 2 eta - 1 (Sec. 3.2, Eq. 8).  REC keeps the roots for the adjoint.
 template <bool REC>
@@ -453,8 +465,8 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
         for (int sv = 0; sv < ns; ++sv) {
             const bool in = inner && sv == 0;
             const float x0 = in ? R.z[1] : far;
-            const float lo = in ? R.z[0] : (left ? far : zb);
-            const float hi = in ? R.z[1] : (left ? zb : far);
+            float lo, hi;
+            root_bracket(R, j, sv, lo, hi);
             const float x = laguerre(R, e, c, x0, lo, hi, !in && left);
             acc += christoffel_weight(R, x);
             if (REC) {   // static indices keep the record in registers
@@ -507,18 +519,6 @@ MB_HD float unpack_query(const float4 v, float y, QueryRec& q) {
     q.x[1] = v.z;
     q.F = 0.0f;
     return v.x;
-}
-
-// Bracket of root sv of a query with j Gauss nodes below it (1 <= j <= 3),
-// as bound_query solves them: the interior root in (z_1, z_2) first when
-// j == 2, then the outer root beyond z_1 (j <= 2) or z_4 (j == 3).
-MB_HD void root_bracket(const Recon& R, int j, int sv, float& lo, float& hi) {
-    const bool left = j <= 2;
-    const float zb = left ? R.z[0] : R.z[3];
-    const float far = left ? zb - R.span : zb + R.span;
-    const bool in = j == 2 && sv == 0;
-    lo = in ? R.z[0] : (left ? far : zb);
-    hi = in ? R.z[1] : (left ? zb : far);
 }
 
 // Compact kept query (8 bytes): {tau, bits}, bits = u_0 | u_1 << 16 with u_r
