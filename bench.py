@@ -502,20 +502,25 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
     torch.cuda.empty_cache()
 
     # batched: all 16 views in one frame (one set of persistent launches over
-    # all views' tiles), the whole step captured in one CUDA graph.  The
-    # bound queries are kept for as many pixels as the free device memory
-    # allows (60 % of it after the workspace); the backward solves the rest
-    # again.
+    # all views' tiles; --batch16-frames F: F frames of 16/F views one after
+    # the other), the whole step captured in one CUDA graph.  The bound
+    # queries are kept for as many pixels as the free device memory allows
+    # (60 % of it after the workspace); the backward solves the rest again.
     counts = [R.pair_counts(g, c) for c in cams]
-    groups = [list(range(len(cams)))]
+    nf = max(1, min(len(cams), getattr(args, "batch16_frames", 1)))
+    groups = [list(range(k * len(cams) // nf, (k + 1) * len(cams) // nf)) for k in range(nf)]
+    gcams = [[cams[i] for i in grp] for grp in groups]
+    gcounts = [R.pair_counts(g, gc) for gc in gcams]
     tp, pp = R.pair_counts(g, cams)
     R.set_query_capacity(0)
-    base = R.workspace_bytes(cams, g.P, tp)
+    base = max(R.workspace_bytes(gc, g.P, gtp) for gc, (gtp, _) in zip(gcams, gcounts))
     torch.cuda.empty_cache()
     free = torch.cuda.mem_get_info(dev)[0]
     R.config.query_budget_gb = max(0.0, 0.6 * (free - base)) / 2 ** 30
-    R.set_query_capacity(pp)
-    need = R.workspace_bytes(cams, g.P, tp)
+    need = 0
+    for gc, (gtp, gpp) in zip(gcams, gcounts):
+        R.set_query_capacity(gpp)
+        need = max(need, R.workspace_bytes(gc, g.P, gtp))
     R._ws = None
     shared = R.workspace(need)
     fbs = [Frame(R, g, [cams[i] for i in grp], target[offs[grp[0]]:offs[grp[-1] + 1]], ws=shared)
@@ -562,7 +567,9 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
                     value=world * tot / (ms * 1e-3) / 1e6, unit="Mpixel/s", ms_per_step=ms, steps=args.steps,
                     sequential_ms_per_step=seq_ms, sequential_mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
                     speedup_vs_sequential=seq_ms / ms, pixels=tot, pixel_pairs=pairs,
-                    query_bytes=8 if R.cfg_c.compact_queries else 16, kept_queries_frac=fbs[0].qcap / max(pp, 1), gpu_launches=int(launches), status=st, clocks=clk)
+                    query_bytes=8 if R.cfg_c.compact_queries else 16,
+                    kept_queries_frac=sum(f.qcap for f in fbs) / max(pp, 1), frames=len(fbs),
+                    gpu_launches=int(launches), status=st, clocks=clk)
 
     # end to end: inputs from pinned host memory into the graph's input
     # buffers, replay, rgb back to host
@@ -600,10 +607,12 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
                 "pixels": tot, "pass": "forward+backward" if with_bwd else "forward",
                 "query_slots": fbs[0].qcap, "pixel_pairs": pp,
                 "kept_queries": "%.0f %% of the pixel pairs (60 %% of free device memory), %d B a query"
-                                % (100.0 * fbs[0].qcap / max(pp, 1), 8 if R.cfg_c.compact_queries else 16),
+                                % (100.0 * sum(f.qcap for f in fbs) / max(pp, 1), 8 if R.cfg_c.compact_queries else 16),
                 "groups": groups,
                 "tiling": dict(tile=list(tuned[:2]), batch=tuned[2], schedule=tuned[3], tuned_ms=tuned[4]),
-                "graph": "whole step in one CUDA graph (one set of persistent launches over all 16 views)",
+                "graph": "whole step in one CUDA graph (%s)" % (
+                    "one set of persistent launches over all 16 views" if len(fbs) == 1 else
+                    "%d frames of %d views, one set of persistent launches each" % (len(fbs), len(cams) // len(fbs))),
                 "l2": "inputs larger than L2",
                 "parallelism": "replicas" if world > 1 else "1 GPU"},
         sequential=dict(ms_per_step=seq_ms, mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
@@ -710,6 +719,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenes.WORKLOADS) + ["batch16", "adc"],
                     help="the default is the headline workload; the others are for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch16-frames", type=int, default=1,
+                    help="batch16: split the 16 views into this many frames run one after the other in the graph")
     ap.add_argument("--no-batch16", action="store_true",
                     help="leave out the short 16-view record the default workload adds to its line")
     ap.add_argument("--forward-only", action="store_true")
