@@ -13,9 +13,10 @@ adjoint).  Prints one JSON line.
 --workload batch16: the same scene seen by 16 views of uneven resolution
 (640x360 / 1280x720 / 1920x1080), the whole fwd+bwd step captured in one
 CUDA graph and replayed, next to 16 sequential single-view render+backward
-calls.  --workload adc: one adaptive-density-control step on the scene's 1M
+calls (--batch16-frames F: F frames of 16/F views one after the other in the
+graph).  --workload adc: one adaptive-density-control step on the scene's 1M
 Gaussians (gradient statistics, then clone / split / prune).  The default
-line carries short records of both.
+line carries short records of both, batch16 as one frame and as two.
 
 With N > 1 (launched by torchrun) every rank renders its own replica of the
 workload (the path has no data exchange); rank 0 prints the aggregate.
@@ -447,6 +448,11 @@ def run_single(args, dist, rank, world, dev):
         R._ws = None
         torch.cuda.empty_cache()
         line["batch16"] = run_batch16(args, None, rank, world, dev, summary=True)
+        # the same 16 views as two frames of 8 in the graph: each frame keeps
+        # all of its bound queries
+        a2 = argparse.Namespace(**vars(args))
+        a2.batch16_frames = 2
+        line["batch16_two_frames"] = run_batch16(a2, None, rank, world, dev, summary=True)
         line["adc"] = run_adc(args, None, rank, world, dev, summary=True)
     return line
 
@@ -562,8 +568,9 @@ def run_batch16(args, dist, rank, world, dev, summary=False):
     pairs = sum(c[1] for c in counts)
     if summary:
         tot = sum(npix)
-        return dict(workload="batch16_shells1M: 16 views (640x360 / 1280x720 / 1920x1080), one frame in one CUDA "
-                             "graph, forward + backward",
+        return dict(workload="batch16_shells1M: 16 views (640x360 / 1280x720 / 1920x1080), %s in one CUDA "
+                             "graph, forward + backward" % ("one frame" if len(fbs) == 1 else
+                                                           "%d frames of %d views" % (len(fbs), len(cams) // len(fbs))),
                     value=world * tot / (ms * 1e-3) / 1e6, unit="Mpixel/s", ms_per_step=ms, steps=args.steps,
                     sequential_ms_per_step=seq_ms, sequential_mpix_s=world * tot / (seq_ms * 1e-3) / 1e6,
                     speedup_vs_sequential=seq_ms / ms, pixels=tot, pixel_pairs=pairs,
