@@ -341,6 +341,15 @@ def run_single(args, dist, rank, world, dev):
     g = GaussianTensors.from_scene(sc, dev)
     target = torch.as_tensor(scenes.target_image(cam.height, cam.width).reshape(-1, 3), device=dev)
     with_bwd = not args.forward_only
+    if with_bwd:
+        # kept bound queries in up to 60 % of the free device memory (the 3M
+        # frame needs 70 GB of them; the library's default budget is 48 GB)
+        tp0, _ = R.pair_counts(g, cam)
+        R.set_query_capacity(0)
+        base = R.workspace_bytes(cam, g.P, tp0)
+        torch.cuda.empty_cache()
+        R.config.query_budget_gb = max(R.config.query_budget_gb,
+                                       0.6 * (torch.cuda.mem_get_info(dev)[0] - base) / 2 ** 30)
     fr = Frame(R, g, cam, target, save_queries=with_bwd)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
