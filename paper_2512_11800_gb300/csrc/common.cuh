@@ -399,8 +399,9 @@ struct QueryRec {
 };
 
 // Bracket of root sv of a query with j Gauss nodes below it (1 <= j <= 3),
-// as bound_query solves them: the interior root in (z_1, z_2) first when
-// j == 2, then the outer root beyond z_1 (j <= 2) or z_4 (j == 3).
+// as bound_query solves them (the same expressions, written inline there):
+// the interior root in (z_1, z_2) first when j == 2, then the outer root
+// beyond z_1 (j <= 2) or z_4 (j == 3).
 MB_HD void root_bracket(const Recon& R, int j, int sv, float& lo, float& hi) {
     const bool left = j <= 2;
     const float zb = left ? R.z[0] : R.z[3];
@@ -461,12 +462,14 @@ MB_HD float bound_query(const Recon& R, float beta, float y_raw, QueryRec* rec) 
         // interior root in (z_1, z_2) approached from z_2 (next to eta's
         // interval) when j == 2, then the outer root left of z_1 (j <= 2) or
         // right of z_4 (j == 3) when K changes sign beyond the nodes.
+        // (root_bracket restates these brackets for the compact kept queries;
+        // here they stay inline, where the loop-invariant parts are hoisted)
 #pragma unroll 1
         for (int sv = 0; sv < ns; ++sv) {
             const bool in = inner && sv == 0;
             const float x0 = in ? R.z[1] : far;
-            float lo, hi;
-            root_bracket(R, j, sv, lo, hi);
+            const float lo = in ? R.z[0] : (left ? far : zb);
+            const float hi = in ? R.z[1] : (left ? zb : far);
             const float x = laguerre(R, e, c, x0, lo, hi, !in && left);
             acc += christoffel_weight(R, x);
             if (REC) {   // static indices keep the record in registers
