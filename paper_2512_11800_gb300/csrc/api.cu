@@ -16,7 +16,7 @@ size_t scan_tmp_elems(int64_t);
 void launch_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t);
 void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaStream_t);
 void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t);
-void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t);
+int launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t);
 int launch_backward_quadrature(const Params&, const ViewTable&, const Layout&, char*, const float*, const float*,
                                const float*,
                                cudaStream_t);
@@ -399,8 +399,9 @@ int mb3dgs_shade(const mb3dgs_config* cfg, const mb3dgs_camera* cams, int n_view
     Ctx c;
     int rc = setup(cfg, cams, n_views, P, pair_capacity, ws_bytes, ws, c);
     if (rc) return rc;
-    launch_shade(c.p, c.vt, c.L, static_cast<char*>(ws), d_rgb, d_T_final, d_penalty,
-                 reinterpret_cast<cudaStream_t>(stream));
+    rc = launch_shade(c.p, c.vt, c.L, static_cast<char*>(ws), d_rgb, d_T_final, d_penalty,
+                      reinterpret_cast<cudaStream_t>(stream));
+    if (rc) return rc;
     return cuda_ok();
 }
 
@@ -419,7 +420,7 @@ int mb3dgs_render(const mb3dgs_config* cfg, const mb3dgs_gaussians* g, const mb3
     if (c.p.schedule == MB3DGS_SCHEDULE_QUEUE) launch_tile_order(c.L, w, st);
     launch_moments(c.p, c.vt, c.L, w, st);
     launch_reconstruct(c.p, c.L, w, nullptr, 0, nullptr, st);
-    launch_shade(c.p, c.vt, c.L, w, d_rgb, d_T_final, d_penalty, st);
+    if ((rc = launch_shade(c.p, c.vt, c.L, w, d_rgb, d_T_final, d_penalty, st))) return rc;
     return cuda_ok();
 }
 

@@ -143,6 +143,51 @@ __device__ __forceinline__ void load_pixel_state(const float* __restrict__ rc, i
 #ifndef MB_SHADE_MIN_CTAS
 #define MB_SHADE_MIN_CTAS 3      // resident CTAs per SM the register budget is sized for
 #endif
+
+// Power-moment and tabulated shading works on (pixel, Gaussian) pairs
+// compacted across the warp.  A rectangle covers on average 3/4 of an 8 x 4
+// footprint it overlaps at 1M Gaussians (2/3 at 200k), so shading record by
+// record leaves a quarter or more of the lanes idle.  Instead the records of
+// a chunk are enumerated in list order, each lane appends the pairs of its own
+// pixel to a per-warp queue, and every full round of 32 queued pairs is shaded
+// with one pair per lane.  The pixel's state (its reconstruction, ray
+// constants and kept-query slot) sits in shared memory for the lane that
+// shades the pair; the pair's O_i and P_i go back through shared memory and
+// the pixel's own lane adds them in list order, so every per-pixel sum is
+// formed from the same terms in the same order as record by record.  The
+// trigonometric node solve diverges too much between Gaussians for mixed
+// rounds to pay: that basis shades record by record.
+template <class RecT>
+struct QueuedShading {
+    static constexpr bool on = true;
+};
+template <>
+struct QueuedShading<TrigRecon> {
+    static constexpr bool on = false;
+};
+
+template <class RecT>
+struct alignas(16) ShadePixel {
+    RecT R;
+    float fpx, fpy, rlen, r2;
+    char* qp;                  // the pixel's kept queries (nullptr: not kept)
+};
+
+template <class RecT>
+struct ShadeWarp {
+    float rec[32 * REC];       // staged records (stage_warp_chunk's layout: records, then their ids)
+    int ids[32];
+    ShadePixel<RecT> pix[32];
+    int ent[64];               // queued pairs: record k of the chunk | pixel lane << 5
+    int ord[64];               // the pair's ordinal among its pixel's pairs (its kept-query slot)
+    float2 res[32];            // O_i and P_i of the round's pairs
+};
+
+template <class RecT>
+constexpr size_t shade_smem_bytes() {
+    return QueuedShading<RecT>::on ? sizeof(ShadeWarp<RecT>) * WARPS : sizeof(float) * WARP_STAGE_FLOATS * WARPS;
+}
+
 template <int NI, bool SAVE, class RecT, int QB = 16>
 __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
                                                const int32_t* __restrict__ ids, const int2* __restrict__ ranges,
@@ -154,7 +199,7 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
                                                const long long* __restrict__ pq_off, char* __restrict__ pq,
                                                int64_t qcap, TableArgs ta) {
     extern __shared__ float4 s_raw[];
-    float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
+    const int lane = threadIdx.x & 31;
     const bool any = sw->n_valid != 0;
     // saved queries: a pixel's pairs from pq_off[pix], N+1 queries of QB bytes
     // each, for the pixels all of whose pairs fit the capacity (a prefix in
@@ -164,9 +209,6 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
     for (int64_t tile = next_unit(ts, true, &fp); tile >= 0; tile = next_unit(ts, false, &fp)) {
         PixelCtx c = unit_ctx(vt, ranges, P, tile, fp, &fx0, &fy0);
         if (!any) c.end = c.start;
-        RecT R;
-        if (c.inside) load_pixel_state(recon, npix, c.pix, ta, R);
-        else R.m0 = 0.0f;
         float S0 = 0.0f, S1 = 0.0f, S2 = 0.0f, O = 0.0f, Pen = 0.0f;
         const float fpx = (float)c.px + 0.5f, fpy = (float)c.py + 0.5f;
         char* qp = nullptr;
@@ -174,19 +216,91 @@ __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, View
             const long long off = pq_off[c.pix];
             if (off + npp[c.pix] <= qcap) qp = pq + (size_t)off * nq * QB;
         }
-        for (int pos = c.start; pos < c.end; pos += 32) {
-            const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
-            if (c.inside) {
-                for (int k = 0; k < m; ++k) {
-                    const float* r = s_buf + k * REC;
-                    if (!rect_contains(r, c.px, c.py)) continue;
-                    const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
-                    const float Oi = pair_quadrature<NI, SAVE, RecT, QB>(p, R, g, &Pen, qp);
-                    if (SAVE && qp) qp += nq * QB;
-                    S0 = fmaf(r[R_RGB + 0], Oi, S0);
-                    S1 = fmaf(r[R_RGB + 1], Oi, S1);
-                    S2 = fmaf(r[R_RGB + 2], Oi, S2);
-                    O += Oi;
+        if constexpr (QueuedShading<RecT>::on) {
+            ShadeWarp<RecT>* W = reinterpret_cast<ShadeWarp<RecT>*>(s_raw) + (threadIdx.x >> 5);
+            const unsigned lanes_below = (1u << lane) - 1u;
+            __syncwarp();                 // the previous unit's pixel states are no longer read
+            {
+                ShadePixel<RecT>& me = W->pix[lane];
+                if (c.inside) load_pixel_state(recon, npix, c.pix, ta, me.R);
+                me.fpx = fpx;
+                me.fpy = fpy;
+                me.rlen = c.rlen;
+                me.r2 = c.r2;
+                me.qp = qp;
+            }
+            int nown = 0;                 // pairs of this lane's pixel queued so far
+            for (int pos = c.start; pos < c.end; pos += 32) {
+                const int m = stage_warp_chunk(W->rec, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
+                int k = 0, pending = 0;
+                unsigned long long mine = 0;  // queue slots holding this lane's pairs
+                for (;;) {
+                    // enqueue records until a round is full (at most 63 pairs queued)
+                    for (; k < m && pending < 32; ++k) {
+                        const bool act = c.inside && rect_contains(W->rec + k * REC, c.px, c.py);
+                        const unsigned mask = __ballot_sync(0xffffffffu, act);
+                        if (act) {
+                            const int slot = pending + __popc(mask & lanes_below);
+                            W->ent[slot] = k | lane << 5;
+                            W->ord[slot] = nown++;
+                            mine |= 1ull << slot;
+                        }
+                        pending += __popc(mask);
+                    }
+                    if (pending == 0) break;
+                    const int n = pending < 32 ? pending : 32;
+                    __syncwarp();         // queued pairs visible to every lane
+                    float Oi = 0.0f, Pi = 0.0f;
+                    if (lane < n) {
+                        const int e = W->ent[lane];
+                        const ShadePixel<RecT>& px = W->pix[e >> 5];
+                        const RecT R = px.R;
+                        const float* r = W->rec + (e & 31) * REC;
+                        const Gauss1D g = pair_gaussian(r, px.fpx - r[R_AX], px.fpy - r[R_AY], px.rlen, px.r2);
+                        char* q = SAVE && px.qp ? px.qp + (size_t)W->ord[lane] * nq * QB : nullptr;
+                        Oi = pair_quadrature<NI, SAVE, RecT, QB>(p, R, g, &Pi, q);
+                    }
+                    W->res[lane] = make_float2(Oi, Pi);
+                    __syncwarp();         // the round's results visible to every lane
+                    for (unsigned own = (unsigned)mine; own != 0u; own &= own - 1u) {
+                        const int s = __ffs(own) - 1;
+                        const float2 v = W->res[s];
+                        const float* r = W->rec + (W->ent[s] & 31) * REC;
+                        S0 = fmaf(r[R_RGB + 0], v.x, S0);
+                        S1 = fmaf(r[R_RGB + 1], v.x, S1);
+                        S2 = fmaf(r[R_RGB + 2], v.x, S2);
+                        O += v.x;
+                        Pen += v.y;
+                    }
+                    // move the pairs queued beyond the round to the front
+                    const int rest = pending - n;
+                    int e2 = 0, o2 = 0;
+                    if (lane < rest) { e2 = W->ent[32 + lane]; o2 = W->ord[32 + lane]; }
+                    __syncwarp();         // every read of slots 0..31 done
+                    if (lane < rest) { W->ent[lane] = e2; W->ord[lane] = o2; }
+                    mine >>= 32;
+                    pending = rest;
+                }
+            }
+        } else {
+            float* s_buf = reinterpret_cast<float*>(s_raw) + (threadIdx.x >> 5) * WARP_STAGE_FLOATS;
+            RecT R;
+            if (c.inside) load_pixel_state(recon, npix, c.pix, ta, R);
+            else R.m0 = 0.0f;
+            for (int pos = c.start; pos < c.end; pos += 32) {
+                const int m = stage_warp_chunk(s_buf, rec, ids, c.rec_base, pos, c.end, fx0, fy0);
+                if (c.inside) {
+                    for (int k = 0; k < m; ++k) {
+                        const float* r = s_buf + k * REC;
+                        if (!rect_contains(r, c.px, c.py)) continue;
+                        const Gauss1D g = pair_gaussian(r, fpx - r[R_AX], fpy - r[R_AY], c.rlen, c.r2);
+                        const float Oi = pair_quadrature<NI, SAVE, RecT, QB>(p, R, g, &Pen, qp);
+                        if (SAVE && qp) qp += nq * QB;
+                        S0 = fmaf(r[R_RGB + 0], Oi, S0);
+                        S1 = fmaf(r[R_RGB + 1], Oi, S1);
+                        S2 = fmaf(r[R_RGB + 2], Oi, S2);
+                        O += Oi;
+                    }
                 }
             }
         }
@@ -246,10 +360,12 @@ void launch_reconstruct(const Params& p, const Layout& L, char* ws, const float*
     }
 }
 
-void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* ws, float* rgb, float* T_final,
-                  float* penalty, cudaStream_t st) {
-    if (L.n_tiles == 0) return;
-    const size_t smem = sizeof(float) * WARP_STAGE_FLOATS * WARPS;
+int launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* ws, float* rgb, float* T_final,
+                 float* penalty, cudaStream_t st) {
+    if (L.n_tiles == 0) return MB3DGS_OK;
+    const size_t smem = p.basis == MB3DGS_BASIS_TRIG ? shade_smem_bytes<TrigRecon>()
+                        : L.tab_m > 0                ? shade_smem_bytes<TabPixel>()
+                                                     : shade_smem_bytes<Recon>();
     const bool save = L.qcap > 0;
     auto kern = p.basis == MB3DGS_BASIS_TRIG
                     ? (save ? (p.n_intervals == 3   ? k_shade<3, true, TrigRecon>
@@ -264,6 +380,7 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
               : p.n_intervals == 3 ? (save ? k_shade<3, true, Recon> : k_shade<3, false, Recon>)
               : p.n_intervals == 5 ? (save ? k_shade<5, true, Recon> : k_shade<5, false, Recon>)
                                    : (save ? k_shade<0, true, Recon> : k_shade<0, false, Recon>);
+    if (!allow_dynamic_smem((const void*)kern, smem)) return MB3DGS_ERR_CUDA;
     const TileLaunch tl = tile_launch(p, L, ws, Q_SHADE, (const void*)kern, smem, st);
     count_launch();
     kern<<<tl.grid, TPB, smem, st>>>(
@@ -276,6 +393,7 @@ void launch_shade(const Params& p, const ViewTable& vt, const Layout& L, char* w
         save ? ws + L.pq : nullptr, L.qcap,
         TableArgs{L.tab_m > 0 ? reinterpret_cast<const float2*>(ws + L.tab) : nullptr,
                   L.tab_m > 0 ? reinterpret_cast<const float*>(ws + L.tab_e) : nullptr, L.tab_m});
+    return MB3DGS_OK;
 }
 
 }  // namespace mb

@@ -35,7 +35,9 @@ size_t scan_tmp_elems(int64_t) { return 0; }
 void launch_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t) {}
 void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaStream_t) {}
 void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t) {}
-void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t) {}
+int launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t) {
+    return 0;
+}
 TileLaunch tile_launch(const Params&, const Layout&, char*, int, const void*, size_t, cudaStream_t) {
     return TileLaunch{};
 }

@@ -31,7 +31,9 @@ size_t scan_tmp_elems(int64_t) { return 0; }
 void launch_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t) {}
 void launch_moments_to_power(const Params&, const Layout&, char*, float*, cudaStream_t) {}
 void launch_reconstruct(const Params&, const Layout&, char*, const float*, int, float*, cudaStream_t) {}
-void launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t) {}
+int launch_shade(const Params&, const ViewTable&, const Layout&, char*, float*, float*, float*, cudaStream_t) {
+    return 0;
+}
 int launch_backward_quadrature(const Params&, const ViewTable&, const Layout&, char*, const float*, const float*,
                                const float*, cudaStream_t) { return 0; }
 int launch_backward_moments(const Params&, const ViewTable&, const Layout&, char*, cudaStream_t) { return 0; }
