@@ -1,11 +1,13 @@
 // Stages 3-5: moment pass, per-pixel reconstruction, quadrature pass.
 //
-// One CTA of 256 threads per tile (one thread per pixel), tiles taken from
-// the schedule of tile.cuh.  The tile's Gaussian list (ascending id) is
-// walked in batches of records staged in shared memory with cp.async; every
-// thread tests its pixel centre against each record's rectangle and
-// accumulates in registers, so per-pixel sums are in a fixed order
-// (deterministic, and the same for every tile shape, batch and schedule).
+// CTAs of 256 threads; every warp takes 8 x 4-pixel footprints of tiles from
+// the schedule of tile.cuh (one lane per pixel) and stages the records of
+// its footprint, in list order (ascending id), into its own shared memory
+// with cp.async.  The moment pass tests each lane's pixel centre against
+// each record's rectangle and accumulates in registers; the quadrature pass
+// queues the pairs and shades them 32 at a time (below).  Either way each
+// pixel sums its Gaussians in list order, so the sums are deterministic and
+// the same for every tile shape, batch and schedule.
 #include "moments.cuh"
 #include "table.cuh"
 #include "tile.cuh"
