@@ -189,6 +189,11 @@ template <class RecT>
 constexpr size_t shade_smem_bytes() {
     return QueuedShading<RecT>::on ? sizeof(ShadeWarp<RecT>) * WARPS : sizeof(float) * WARP_STAGE_FLOATS * WARPS;
 }
+// MB_SHADE_MIN_CTAS CTAs must fit the SM's 228 KB of shared memory (1 KB of
+// it reserved per CTA) for the register budget of __launch_bounds__ to pay.
+static_assert(MB_SHADE_MIN_CTAS * (shade_smem_bytes<Recon>() + 1024) <= 228 * 1024 &&
+                  MB_SHADE_MIN_CTAS * (shade_smem_bytes<TabPixel>() + 1024) <= 228 * 1024,
+              "queued shading: shared memory per CTA too large for the resident CTAs");
 
 template <int NI, bool SAVE, class RecT, int QB = 16>
 __global__ void __launch_bounds__(TPB, MB_SHADE_MIN_CTAS) k_shade(Params p, ViewTable vt, TileSched ts, const float* __restrict__ rec,
